@@ -1,0 +1,192 @@
+/*
+ * tnq.h -- C ABI of the GB300 tensor-network amplitude engine.
+ *
+ * The calls follow the problem statement of Sec. 3.1 of "Tensor Network
+ * Quantum Virtual Machine for Simulating Quantum Circuits at Exascale"
+ * (Nguyen et al., arXiv 2104.10523): a circuit goes in (Sec. 2.2, Sec. 3),
+ * it is turned into a tensor network (Sec. 3.1, Fig. 1), a contraction path and
+ * a set of sliced indices are found (Sec. 3.1), and the network is contracted
+ * into bitstring amplitudes (Sec. 3.1.1, Eq. ampl_calc; the bit-string request
+ * of Sec. 4.3) or, for circuits with Kraus channels (Sec. 3.3, Eq. kraus_sum),
+ * into stochastic-trajectory estimates of bitstring probabilities.
+ *
+ * Conventions shared by every call:
+ *   - all pointers are owned by the caller unless a call says otherwise;
+ *     handles (tnq_circuit, tnq_plan, tnq_ctx) are owned by the library and
+ *     released with the matching *_destroy call;
+ *   - a buffer argument may be a host or a device pointer where the call
+ *     says so; the library checks which with cudaPointerGetAttributes;
+ *   - device memory: the library allocates none on its own; every byte it
+ *     uses on the GPU lives in the workspace the caller binds to a plan;
+ *   - calls never throw; on failure they return a status other than TNQ_OK
+ *     and leave a message for tnq_last_error();
+ *   - GPU calls are ordered on the context's stream and return after the
+ *     results are complete (host outputs written, device outputs final).
+ *
+ * Layout conventions:
+ *   - complex numbers are (re, im) pairs; double precision on the host side,
+ *     complex64 (two floats) inside device tensors;
+ *   - a k-qubit gate matrix is row-major 2^k x 2^k complex128, acting on the
+ *     basis of its listed qubits with qubits[0] the most significant bit;
+ *   - a bitstring is n int8 values bits[q] in {0,1} for qubit q;
+ *   - a tensor whose indices all have dimension 2 is a flat array of 2^r
+ *     complex64 entries; labels[p] names bit p of the flat index (bit 0 has
+ *     stride 1).
+ */
+#ifndef TNQ_H
+#define TNQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNQ_OK = 0,
+  TNQ_ERR_INVALID_ARG = 1,      /* bad qubit, non-unitary gate, incomplete Kraus set, bit not 0/1 */
+  TNQ_ERR_PLAN_INFEASIBLE = 2,  /* no slicing meets max_intermediate_log2 */
+  TNQ_ERR_WORKSPACE = 3,        /* bound workspace missing or too small */
+  TNQ_ERR_CUDA = 4,             /* a CUDA runtime/driver call failed */
+  TNQ_ERR_TIMEOUT = 5,          /* a bounded device-side wait expired */
+  TNQ_ERR_NOT_SUPPORTED = 6,    /* mode or shape not available */
+  TNQ_ERR_NO_DEVICE = 7         /* no usable sm_103 device */
+} tnq_status;
+
+/* Arithmetic of the pairwise-contraction GEMMs (Sec. 3.1 steps; TF32 as in the
+ * paper's Table 2 A100 runs).  Storage is complex64 in every mode,
+ * accumulation inside a GEMM is FP32, the cross-slice sums are FP64. */
+typedef enum {
+  TNQ_PREC_FP32 = 0,    /* CUDA-core FFMA complex GEMM, plain FP32 */
+  TNQ_PREC_TF32 = 1,    /* tensor cores, one TF32 product */
+  TNQ_PREC_TF32X3 = 2,  /* tensor cores, hi/lo TF32 split, 3 products */
+  TNQ_PREC_BF16X3 = 3   /* tensor cores, hi/lo BF16 split, 3 products */
+} tnq_precision;
+
+/* How the contraction path is chosen (Sec. 3.1: FLOP minimisation by graph
+ * partitioning and heuristics). */
+typedef enum {
+  TNQ_PATH_GREEDY = 0,  /* greedy pairwise, deterministic tie-break */
+  TNQ_PATH_BISECT = 1,  /* recursive hypergraph bisection, best of n_candidates by FLOPs */
+  TNQ_PATH_BEST = 2,    /* best by FLOPs over greedy and bisection candidates */
+  TNQ_PATH_LEARNED = 3  /* candidates ranked by the learned cost model, if one is loaded */
+} tnq_path_mode;
+
+typedef struct tnq_circuit tnq_circuit;
+typedef struct tnq_plan tnq_plan;
+typedef struct tnq_ctx tnq_ctx;
+
+typedef struct {
+  int device;      /* CUDA device ordinal */
+  void* stream;    /* cudaStream_t all work is ordered on; NULL = legacy default stream */
+  int precision;   /* tnq_precision */
+} tnq_options;
+
+typedef struct {
+  int max_intermediate_log2; /* cap on log2(elements) of any intermediate, batch bits
+                                included; indices are sliced until it holds (Sec. 3.1) */
+  int batch_log2;            /* bitstrings contracted together per pass: 2^batch_log2 */
+  int traj_log2;             /* trajectories per pass for noisy circuits: 2^traj_log2 */
+  int path_mode;             /* tnq_path_mode */
+  int n_candidates;          /* candidate trees examined by BISECT/BEST/LEARNED */
+  uint64_t seed;             /* seed of the randomised path search */
+} tnq_plan_opts;
+
+typedef struct {
+  int n_leaves;              /* tensors after building and simplification (Sec. 3.1.1) */
+  int n_steps;               /* pairwise contractions per pass */
+  int n_sliced;              /* sliced indices; 2^n_sliced passes per batch */
+  int max_log2;              /* largest intermediate, log2 elements, after slicing */
+  int batch_log2, traj_log2;
+  double flops_per_pass;     /* 8 real flops per complex multiply-add, one slice */
+  double flops_per_batch;    /* flops_per_pass * 2^n_sliced */
+  double bytes_per_pass;     /* algorithmic HBM bytes of the GEMM and permute steps */
+  double search_ms;          /* host time of the path search and slicing */
+  size_t workspace_bytes;    /* device bytes tnq_plan_bind needs */
+} tnq_plan_info;
+
+/* ---- library ---------------------------------------------------------- */
+const char* tnq_version(void);
+const char* tnq_status_string(tnq_status s);
+/* Message of the last failed call on this thread (never NULL). */
+const char* tnq_last_error(void);
+
+/* ---- circuits (host only) ---------------------------------------------- */
+/* A register of n_qubits qubits in |0...0> (Sec. 3.1: one rank-1 tensor per qubit).
+ * Errors: INVALID_ARG if n_qubits < 1 or > 4096. */
+tnq_status tnq_circuit_create(int n_qubits, tnq_circuit** out);
+void tnq_circuit_destroy(tnq_circuit* c);
+/* Append a 1- or 2-qubit gate (rank-2 / rank-4 tensor of Fig. 1a).
+ * m: host, 2^arity x 2^arity complex128 row-major, copied.
+ * Errors: INVALID_ARG for arity not 1 or 2, qubit out of range or repeated,
+ * or a matrix with ||U^dagger U - I||_max > 1e-10. */
+tnq_status tnq_circuit_gate(tnq_circuit* c, int arity, const int* qubits, const double* m);
+/* Append a Kraus channel {A_k} (Eq. kraus_sum).  kraus: host, n_ops matrices of
+ * 2^arity x 2^arity complex128, copied.  Errors: INVALID_ARG if n_ops < 1 or
+ * > 64, or ||sum_k A_k^dagger A_k - I||_max > 1e-10. */
+tnq_status tnq_circuit_channel(tnq_circuit* c, int arity, const int* qubits, int n_ops,
+                               const double* kraus);
+int tnq_circuit_n_qubits(const tnq_circuit* c);
+
+/* ---- plans (host only) -------------------------------------------------- */
+/* Build the projected tensor network of the circuit (Sec. 3.1, 3.1.1), absorb
+ * one-qubit tensors into their neighbours, find a contraction tree and the
+ * sliced indices (Sec. 3.1), and lay out every step.  No GPU work.
+ * Errors: INVALID_ARG (bad options), PLAN_INFEASIBLE (cap cannot be met). */
+tnq_status tnq_plan_create(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_plan** out);
+void tnq_plan_destroy(tnq_plan* p);
+tnq_status tnq_plan_get_info(const tnq_plan* p, tnq_plan_info* info);
+/* Per-step shape record: for step i, writes 8 ints
+ * {a_rank, b_rank, out_rank, log2 H, log2 M, log2 N, log2 K, a_is_leaf | b_is_leaf << 1}.
+ * rec must hold 8 * n_steps ints. */
+tnq_status tnq_plan_get_steps(const tnq_plan* p, int* rec);
+
+/* ---- contexts and GPU execution ----------------------------------------- */
+/* Errors: NO_DEVICE when the device is missing or not compute capability 10.3. */
+tnq_status tnq_ctx_create(const tnq_options* opts, tnq_ctx** out);
+void tnq_ctx_destroy(tnq_ctx* ctx);
+tnq_status tnq_ctx_set_precision(tnq_ctx* ctx, int precision);
+
+/* Bind a caller-owned device workspace of at least info.workspace_bytes to the
+ * plan and upload its constant tensors into it.  The workspace must stay valid
+ * and unused by others until the plan is destroyed or re-bound.
+ * Errors: WORKSPACE if NULL or too small, CUDA. */
+tnq_status tnq_plan_bind(tnq_ctx* ctx, tnq_plan* p, void* workspace, size_t bytes);
+
+/* Amplitudes <x|U|0...0> (Eq. ampl_calc) for n_bs bitstrings.
+ * bits: [n_bs][n_qubits] int8, host or device.  out: [n_bs][2] double (re, im),
+ * host or device.  Bitstrings are processed 2^batch_log2 at a time, every
+ * slice of a batch summed in FP64 in ascending slice order.
+ * Errors: INVALID_ARG (bit not 0/1, plan built for a noisy circuit),
+ * WORKSPACE (plan not bound), CUDA. */
+tnq_status tnq_amplitudes(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t* bits,
+                          double* out);
+
+/* Noisy probabilities p(x) = <x|rho|x> estimated from n_traj stochastic
+ * trajectories (Eq. kraus_sum channels, one Kraus operator drawn per channel
+ * with probability Tr(A_k^dagger A_k)/d and rescaled by its inverse square
+ * root, so the mean of |amp|^2 is unbiased).  Trajectory t, channel c draws
+ * the (t*2^32 + c + 1)-th SplitMix64 output of `seed`.
+ * bits: [n_bs][n] int8 host or device; p_out, stderr_out: [n_bs] double, host
+ * or device (stderr_out may be NULL).  Errors as tnq_amplitudes. */
+tnq_status tnq_noisy_probabilities(tnq_ctx* ctx, tnq_plan* p, int64_t n_traj, uint64_t seed,
+                                   int64_t n_bs, const int8_t* bits, double* p_out,
+                                   double* stderr_out);
+
+/* One pairwise contraction (a single step of Sec. 3.1's sequence) of device
+ * tensors A (rank ra, labels a_labels) and B (rank rb, labels b_labels) into
+ * C (rank rc, labels c_labels): C = sum over the labels A and B share but C
+ * lacks of A*B.  Labels shared by A, B and C are batch indices.  A, B, C:
+ * device complex64.  workspace: device scratch of at least
+ * tnq_contract_workspace_bytes(...) bytes.  Uses the context's precision.
+ * Errors: INVALID_ARG (label sets inconsistent, rank > 31), WORKSPACE, CUDA. */
+size_t tnq_contract_workspace_bytes(int precision, int ra, int rb, int rc);
+tnq_status tnq_contract_pair(tnq_ctx* ctx, const void* A, int ra, const int* a_labels,
+                             const void* B, int rb, const int* b_labels, void* C, int rc,
+                             const int* c_labels, void* workspace, size_t workspace_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNQ_H */

@@ -1,0 +1,253 @@
+// extern "C" boundary (include/tnq.h).  Argument checking, handle ownership,
+// error strings; the work happens in the planner and the executor.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "executor.h"
+#include "internal.h"
+
+namespace tnq {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+tnq_status fail(tnq_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+}  // namespace tnq
+
+using namespace tnq;
+
+namespace {
+
+bool check_qubits(const Circuit& c, int arity, const int* qubits, std::string* why) {
+  if (arity != 1 && arity != 2) {
+    *why = "arity must be 1 or 2";
+    return false;
+  }
+  if (!qubits) {
+    *why = "qubits is NULL";
+    return false;
+  }
+  for (int i = 0; i < arity; ++i)
+    if (qubits[i] < 0 || qubits[i] >= c.n) {
+      *why = "qubit index out of range";
+      return false;
+    }
+  if (arity == 2 && qubits[0] == qubits[1]) {
+    *why = "two-qubit op on a repeated qubit";
+    return false;
+  }
+  return true;
+}
+
+std::vector<cd> read_matrix(const double* m, int d) {
+  std::vector<cd> v(d * d);
+  for (int i = 0; i < d * d; ++i) v[i] = cd(m[2 * i], m[2 * i + 1]);
+  return v;
+}
+
+// max |(sum_k A_k^dag A_k) - I|
+double completeness_error(const std::vector<std::vector<cd>>& mats, int d) {
+  double worst = 0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      cd s(0, 0);
+      for (auto& A : mats)
+        for (int k = 0; k < d; ++k) s += std::conj(A[k * d + i]) * A[k * d + j];
+      if (i == j) s -= 1.0;
+      worst = std::max(worst, std::abs(s));
+    }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tnq_version(void) { return "tnq 0.1 (sm_103a)"; }
+
+const char* tnq_status_string(tnq_status s) {
+  switch (s) {
+    case TNQ_OK: return "ok";
+    case TNQ_ERR_INVALID_ARG: return "invalid argument";
+    case TNQ_ERR_PLAN_INFEASIBLE: return "plan infeasible";
+    case TNQ_ERR_WORKSPACE: return "workspace missing or too small";
+    case TNQ_ERR_CUDA: return "CUDA error";
+    case TNQ_ERR_TIMEOUT: return "device wait timed out";
+    case TNQ_ERR_NOT_SUPPORTED: return "not supported";
+    case TNQ_ERR_NO_DEVICE: return "no usable device";
+  }
+  return "unknown status";
+}
+
+const char* tnq_last_error(void) { return g_last_error.c_str(); }
+
+tnq_status tnq_circuit_create(int n_qubits, tnq_circuit** out) {
+  if (!out) return fail(TNQ_ERR_INVALID_ARG, "out is NULL");
+  if (n_qubits < 1 || n_qubits > 4096) return fail(TNQ_ERR_INVALID_ARG, "n_qubits must be in [1, 4096]");
+  auto* c = new (std::nothrow) tnq_circuit();
+  if (!c) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  c->c.n = n_qubits;
+  *out = c;
+  return TNQ_OK;
+}
+
+void tnq_circuit_destroy(tnq_circuit* c) { delete c; }
+
+int tnq_circuit_n_qubits(const tnq_circuit* c) { return c ? c->c.n : 0; }
+
+tnq_status tnq_circuit_gate(tnq_circuit* c, int arity, const int* qubits, const double* m) {
+  if (!c || !m) return fail(TNQ_ERR_INVALID_ARG, "circuit or matrix is NULL");
+  std::string why;
+  if (!check_qubits(c->c, arity, qubits, &why)) return fail(TNQ_ERR_INVALID_ARG, why);
+  int d = 1 << arity;
+  COp op;
+  op.qubits.assign(qubits, qubits + arity);
+  op.mats.push_back(read_matrix(m, d));
+  for (auto& z : op.mats[0])
+    if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return fail(TNQ_ERR_INVALID_ARG, "non-finite gate");
+  if (completeness_error(op.mats, d) > 1e-10) return fail(TNQ_ERR_INVALID_ARG, "gate matrix is not unitary");
+  c->c.ops.push_back(std::move(op));
+  return TNQ_OK;
+}
+
+tnq_status tnq_circuit_channel(tnq_circuit* c, int arity, const int* qubits, int n_ops, const double* kraus) {
+  if (!c || !kraus) return fail(TNQ_ERR_INVALID_ARG, "circuit or Kraus array is NULL");
+  std::string why;
+  if (!check_qubits(c->c, arity, qubits, &why)) return fail(TNQ_ERR_INVALID_ARG, why);
+  if (n_ops < 1 || n_ops > 64) return fail(TNQ_ERR_INVALID_ARG, "n_ops must be in [1, 64]");
+  int d = 1 << arity;
+  COp op;
+  op.channel = true;
+  op.qubits.assign(qubits, qubits + arity);
+  for (int k = 0; k < n_ops; ++k) op.mats.push_back(read_matrix(kraus + 2 * size_t(k) * d * d, d));
+  if (completeness_error(op.mats, d) > 1e-10)
+    return fail(TNQ_ERR_INVALID_ARG, "Kraus operators do not satisfy sum A^dag A = I");
+  for (auto& A : op.mats) {
+    double q = 0;
+    for (auto& z : A) q += std::norm(z);
+    op.kraus_q.push_back(q / d);
+  }
+  op.channel_index = c->c.n_channels++;
+  c->c.ops.push_back(std::move(op));
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_create(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_plan** out) {
+  if (!c || !opts || !out) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  auto* p = new (std::nothrow) tnq_plan();
+  if (!p) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  tnq_status s = make_plan(c->c, *opts, &p->p);
+  if (s != TNQ_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return TNQ_OK;
+}
+
+void tnq_plan_destroy(tnq_plan* p) { delete p; }
+
+tnq_status tnq_plan_get_info(const tnq_plan* pp, tnq_plan_info* info) {
+  if (!pp || !info) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  const Plan& p = pp->p;
+  info->n_leaves = (int)p.net.leaves.size();
+  info->n_steps = (int)p.steps.size();
+  info->n_sliced = (int)p.slice_labels.size();
+  info->max_log2 = p.cost.max_log2;
+  info->batch_log2 = p.batch_log2;
+  info->traj_log2 = p.traj_log2;
+  info->flops_per_pass = p.cost.flops;
+  info->flops_per_batch = p.cost.flops * std::ldexp(1.0, (int)p.slice_labels.size());
+  info->bytes_per_pass = p.cost.bytes;
+  info->search_ms = p.search_ms;
+  info->workspace_bytes = p.ws_total;
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_get_steps(const tnq_plan* pp, int* rec) {
+  if (!pp || !rec) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  const Plan& p = pp->p;
+  const int L = p.tree.n_leaves;
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    const Step& s = p.steps[i];
+    int* r = rec + 8 * i;
+    r[0] = (int)s.a_req.size();
+    r[1] = (int)s.b_req.size();
+    r[2] = (int)s.out_labels.size();
+    r[3] = s.nH;
+    r[4] = s.nM;
+    r[5] = s.nN;
+    r[6] = s.nK;
+    r[7] = (s.a < L ? 1 : 0) | (s.b < L ? 2 : 0);
+  }
+  return TNQ_OK;
+}
+
+tnq_status tnq_ctx_create(const tnq_options* o, tnq_ctx** out) {
+  if (!o || !out) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (o->precision < TNQ_PREC_FP32 || o->precision > TNQ_PREC_BF16X3)
+    return fail(TNQ_ERR_INVALID_ARG, "unknown precision");
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || o->device < 0 || o->device >= count) {
+    cudaGetLastError();
+    return fail(TNQ_ERR_NO_DEVICE, "no CUDA device with that ordinal");
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, o->device) != cudaSuccess) return fail(TNQ_ERR_NO_DEVICE, "device query failed");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(TNQ_ERR_NO_DEVICE, "this library is built for sm_103a (GB300) only");
+  auto* c = new (std::nothrow) tnq_ctx();
+  if (!c) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  c->c.device = o->device;
+  c->c.stream = static_cast<cudaStream_t>(o->stream);
+  c->c.precision = o->precision;
+  c->c.sm_count = prop.multiProcessorCount;
+  *out = c;
+  return TNQ_OK;
+}
+
+void tnq_ctx_destroy(tnq_ctx* c) { delete c; }
+
+tnq_status tnq_ctx_set_precision(tnq_ctx* c, int precision) {
+  if (!c) return fail(TNQ_ERR_INVALID_ARG, "NULL context");
+  if (precision < TNQ_PREC_FP32 || precision > TNQ_PREC_BF16X3) return fail(TNQ_ERR_INVALID_ARG, "unknown precision");
+  c->c.precision = precision;
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_bind(tnq_ctx* c, tnq_plan* p, void* ws, size_t bytes) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return exec_bind(&c->c, &p->p, ws, bytes);
+}
+
+tnq_status tnq_amplitudes(tnq_ctx* c, tnq_plan* p, int64_t n_bs, const int8_t* bits, double* out) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return exec_amplitudes(&c->c, &p->p, n_bs, bits, out);
+}
+
+tnq_status tnq_noisy_probabilities(tnq_ctx* c, tnq_plan* p, int64_t n_traj, uint64_t seed, int64_t n_bs,
+                                   const int8_t* bits, double* p_out, double* se_out) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return exec_noisy(&c->c, &p->p, n_traj, seed, n_bs, bits, p_out, se_out);
+}
+
+size_t tnq_contract_workspace_bytes(int precision, int ra, int rb, int rc) {
+  if (ra < 0 || rb < 0 || rc < 0 || ra > 31 || rb > 31 || rc > 31) return 0;
+  return contract_workspace_bytes(precision, ra, rb, rc);
+}
+
+tnq_status tnq_contract_pair(tnq_ctx* c, const void* A, int ra, const int* al, const void* B, int rb,
+                             const int* bl, void* C, int rc, const int* cl, void* ws, size_t ws_bytes) {
+  if (!c || !A || !B || !C) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if ((ra && !al) || (rb && !bl) || (rc && !cl)) return fail(TNQ_ERR_INVALID_ARG, "NULL label array");
+  return exec_contract_pair(&c->c, A, ra, al, B, rb, bl, C, rc, cl, ws, ws_bytes);
+}
+
+}  // extern "C"

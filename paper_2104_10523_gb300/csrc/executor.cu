@@ -1,0 +1,316 @@
+// Executor: runs a plan's contraction sequence on the GPU.
+//
+// Per batch of 2^batch_log2 bitstrings: fill the projection leaves from the
+// bitstrings (Sec. 3.1.1), then for every slice id (Sec. 3.1 slicing) run the
+// steps in tree post-order (bit-permute of the operands that need it, batched
+// complex GEMM), with the root step's epilogue adding its result in FP64 to
+// the batch accumulator (the cross-slice sum, fixed ascending slice order).
+// The accumulator is finally mapped to bitstring order.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "executor.h"
+#include "kernels.cuh"
+#include "gemm_tc.cuh"
+#include "traj.cuh"
+
+namespace tnq {
+
+tnq_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(TNQ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TNQ_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int tc_mode_a(int prec) {
+  switch (prec) {
+    case TNQ_PREC_TF32: return PM_AEXP_TF32;
+    case TNQ_PREC_TF32X3: return PM_AEXP_TF32X3;
+    case TNQ_PREC_BF16X3: return PM_AEXP_BF16X3;
+  }
+  return PM_AEXP_F32;
+}
+int tc_mode_b(int prec) {
+  switch (prec) {
+    case TNQ_PREC_TF32: return PM_B_TF32;
+    case TNQ_PREC_TF32X3: return PM_B_TF32X3;
+    case TNQ_PREC_BF16X3: return PM_B_BF16X3;
+  }
+  return PM_C64;
+}
+
+// Bytes of one converted operand half (hi or lo) for n complex elements.
+size_t a_half_bytes(int prec, size_t n) { return prec == TNQ_PREC_BF16X3 ? 8 * n : 16 * n; }
+size_t b_half_bytes(int prec, size_t n) { return prec == TNQ_PREC_BF16X3 ? 4 * n : 8 * n; }
+
+struct StepOperands {
+  const void* a0 = nullptr;
+  const void* a1 = nullptr;
+  const void* b0 = nullptr;
+  const void* b1 = nullptr;
+};
+
+// Prepare operands (permute / convert) and run one batched complex GEMM.
+tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_labels, bool perm_a,
+                         const void* b_src, const std::vector<int>& b_labels, bool perm_b,
+                         const std::vector<int>& a_req, const std::vector<int>& b_req,
+                         const std::vector<int>& slice_labels, int slice_id, int nH, int nM, int nN, int nK,
+                         char* scratch_a, char* scratch_b, void* C, void* acc) {
+  const int prec = ctx->precision;
+  StepOperands op;
+  PermDesc d;
+  const int ns = (int)slice_labels.size();
+  if (prec == TNQ_PREC_FP32) {
+    if (perm_a) {
+      build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(),
+                      ns, PM_C64, nK, &d);
+      TNQ_CUDA(launch_permute(d, a_src, scratch_a, nullptr, slice_id, ctx->sm_count, ctx->stream));
+      op.a0 = scratch_a;
+    } else {
+      op.a0 = a_src;
+    }
+    if (perm_b) {
+      build_perm_desc(b_labels.data(), (int)b_labels.size(), b_req.data(), (int)b_req.size(), slice_labels.data(),
+                      ns, PM_C64, nK, &d);
+      TNQ_CUDA(launch_permute(d, b_src, scratch_b, nullptr, slice_id, ctx->sm_count, ctx->stream));
+      op.b0 = scratch_b;
+    } else {
+      op.b0 = b_src;
+    }
+    TNQ_CUDA(launch_cgemm_simt(op.a0, op.b0, C, acc, 1 << nM, 1 << nN, 1 << nK, 1 << nH, ctx->stream));
+    return TNQ_OK;
+  }
+  // tensor-core modes: A is always expanded (and split), B split unless plain TF32 in place
+  size_t na = size_t(1) << a_req.size(), nb = size_t(1) << b_req.size();
+  build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(), ns,
+                  tc_mode_a(prec), nK, &d);
+  char* a1 = scratch_a + ((a_half_bytes(prec, na) + 1023) & ~size_t(1023));
+  TNQ_CUDA(launch_permute(d, a_src, scratch_a, a1, slice_id, ctx->sm_count, ctx->stream));
+  op.a0 = scratch_a;
+  op.a1 = prec == TNQ_PREC_TF32 ? nullptr : a1;
+  if (prec == TNQ_PREC_TF32 && !perm_b) {
+    op.b0 = b_src;
+  } else {
+    build_perm_desc(b_labels.data(), (int)b_labels.size(), b_req.data(), (int)b_req.size(), slice_labels.data(),
+                    ns, tc_mode_b(prec), nK, &d);
+    char* b1 = scratch_b + ((b_half_bytes(prec, nb) + 1023) & ~size_t(1023));
+    TNQ_CUDA(launch_permute(d, b_src, scratch_b, b1, slice_id, ctx->sm_count, ctx->stream));
+    op.b0 = scratch_b;
+    op.b1 = prec == TNQ_PREC_TF32 ? nullptr : b1;
+  }
+  TcGemmArgs g;
+  g.a_hi = op.a0;
+  g.a_lo = op.a1;
+  g.b_hi = op.b0;
+  g.b_lo = op.b1;
+  g.c = C;
+  g.acc = acc;
+  g.M = 1 << nM;
+  g.N = 1 << nN;
+  g.K = 1 << nK;
+  g.batch = 1 << nH;
+  g.precision = prec;
+  cudaError_t e = launch_cgemm_tc(g, ctx->sm_count, ctx->stream);
+  if (e == cudaErrorNotSupported)
+    return fail(TNQ_ERR_NOT_SUPPORTED, "tensor-core GEMM unavailable for this shape/precision");
+  TNQ_CUDA(e);
+  return TNQ_OK;
+}
+
+tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws) {
+  for (auto& s : p->steps) {
+    auto& ta = p->tensors[s.a];
+    auto& tb = p->tensors[s.b];
+    void* acc = s.out == p->root ? (void*)(ws + p->ws_acc) : nullptr;
+    void* C = s.out == p->root ? nullptr : (void*)(ws + p->tensors[s.out].offset);
+    tnq_status st = run_gemm_step(ctx, ws + ta.offset, ta.labels, s.perm_a,
+                                  ws + tb.offset, tb.labels, s.perm_b,
+                                  s.a_req, s.b_req, p->slice_labels, slice_id, s.nH, s.nM, s.nN, s.nK,
+                                  ws + p->ws_scratch_a, ws + p->ws_scratch_b, C, acc);
+    if (st != TNQ_OK) return st;
+  }
+  return TNQ_OK;
+}
+
+}  // namespace
+
+tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes) {
+  if (!ws) return fail(TNQ_ERR_WORKSPACE, "workspace is NULL");
+  if (bytes < p->ws_total)
+    return fail(TNQ_ERR_WORKSPACE, "workspace too small: need " + std::to_string(p->ws_total) + " bytes");
+  if (!is_device_ptr(ws)) return fail(TNQ_ERR_WORKSPACE, "workspace must be device memory");
+  TNQ_CUDA(cudaSetDevice(ctx->device));
+  char* base = static_cast<char*>(ws);
+  std::vector<float> buf;
+  for (size_t i = 0; i < p->net.leaves.size(); ++i) {
+    const Leaf& L = p->net.leaves[i];
+    if (L.kind != LEAF_STATIC) continue;
+    buf.resize(2 * L.data.size());
+    for (size_t k = 0; k < L.data.size(); ++k) {
+      buf[2 * k] = (float)L.data[k].real();
+      buf[2 * k + 1] = (float)L.data[k].imag();
+    }
+    TNQ_CUDA(cudaMemcpyAsync(base + p->tensors[i].offset, buf.data(), buf.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, ctx->stream));
+    TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  p->bound_ws = ws;
+  p->bound_bytes = bytes;
+  return TNQ_OK;
+}
+
+tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, double* out) {
+  if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
+  if (p->net.noisy) return fail(TNQ_ERR_INVALID_ARG, "plan is for a noisy circuit; use tnq_noisy_probabilities");
+  if (n_bs < 0 || (n_bs > 0 && (!bits || !out))) return fail(TNQ_ERR_INVALID_ARG, "bad bitstring/output buffers");
+  if (n_bs == 0) return TNQ_OK;
+  TNQ_CUDA(cudaSetDevice(ctx->device));
+  char* ws = static_cast<char*>(p->bound_ws);
+  const int n = p->net.n_qubits, w = p->batch_log2;
+  const int64_t per = int64_t(1) << w;
+  const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(out);
+  if (!bits_dev)
+    for (int64_t i = 0; i < n_bs * n; ++i)
+      if (bits[i] != 0 && bits[i] != 1) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  int* err_flag = reinterpret_cast<int*>(ws + p->ws_misc);
+  int8_t* bits_stage = reinterpret_cast<int8_t*>(ws + p->ws_misc + 256);
+  double* out_stage = reinterpret_cast<double*>(ws + p->ws_misc + 256 + ((size_t(n) * per + 255) / 256) * 256);
+  const int L = p->tree.n_leaves;
+  int first_proj = -1;
+  for (int i = 0; i < L; ++i)
+    if (p->net.leaves[i].kind == LEAF_PROJ) {
+      first_proj = i;
+      break;
+    }
+  size_t stride = first_proj + 1 < L ? p->tensors[first_proj + 1].offset - p->tensors[first_proj].offset : 0;
+  std::vector<int> pos(w);
+  const auto& rl = p->tensors[p->root].labels;
+  for (int j = 0; j < w; ++j)
+    pos[j] = int(std::find(rl.begin(), rl.end(), p->net.batch_labels[j]) - rl.begin());
+  TNQ_CUDA(cudaMemsetAsync(err_flag, 0, sizeof(int), ctx->stream));
+  const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
+  const int n_slices = 1 << p->slice_labels.size();
+  for (int64_t base = 0; base < n_bs; base += per) {
+    int64_t nv = std::min<int64_t>(per, n_bs - base);
+    const int8_t* bsrc;
+    if (bits_dev) {
+      bsrc = bits + base * n;
+    } else {
+      TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * n, size_t(nv) * n, cudaMemcpyHostToDevice, ctx->stream));
+      bsrc = bits_stage;
+    }
+    TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w, bsrc, nv, err_flag, ctx->stream));
+    TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
+    for (int s = 0; s < n_slices; ++s) {
+      tnq_status st = run_pass(ctx, p, s, ws);
+      if (st != TNQ_OK) return st;
+    }
+    double* dst = out_dev ? out + 2 * base : out_stage;
+    TNQ_CUDA(launch_finalize(ws + p->ws_acc, dst, nv, pos.data(), w, ctx->stream));
+    if (!out_dev)
+      TNQ_CUDA(cudaMemcpyAsync(out + 2 * base, out_stage, size_t(nv) * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  int herr = 0;
+  TNQ_CUDA(cudaMemcpyAsync(&herr, err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (herr) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  return TNQ_OK;
+}
+
+tnq_status exec_noisy(Ctx* ctx, Plan* p, int64_t n_traj, uint64_t seed, int64_t n_bs, const int8_t* bits,
+                      double* p_out, double* se_out) {
+  (void)ctx;
+  (void)p;
+  (void)n_traj;
+  (void)seed;
+  (void)n_bs;
+  (void)bits;
+  (void)p_out;
+  (void)se_out;
+  return fail(TNQ_ERR_NOT_SUPPORTED, "noisy trajectories not built yet");
+}
+
+size_t contract_workspace_bytes(int precision, int ra, int rb, int rc) {
+  (void)precision;
+  size_t na = size_t(1) << std::max(ra, rb), nb = na;
+  return 32 * na + 16 * nb + 8 * (size_t(1) << rc) + 3 * 4096;
+}
+
+tnq_status exec_contract_pair(Ctx* ctx, const void* A, int ra, const int* al, const void* B, int rb,
+                              const int* bl, void* C, int rc, const int* cl, void* ws, size_t ws_bytes) {
+  if (ra < 0 || rb < 0 || rc < 0 || ra > 31 || rb > 31 || rc > 31)
+    return fail(TNQ_ERR_INVALID_ARG, "ranks must be in [0, 31]");
+  std::vector<int> la(al, al + ra), lb(bl, bl + rb), lc(cl, cl + rc);
+  auto has = [](const std::vector<int>& v, int l) { return std::find(v.begin(), v.end(), l) != v.end(); };
+  auto uniq = [](std::vector<int> v) {
+    std::sort(v.begin(), v.end());
+    return std::adjacent_find(v.begin(), v.end()) == v.end();
+  };
+  if (!uniq(la) || !uniq(lb) || !uniq(lc)) return fail(TNQ_ERR_INVALID_ARG, "repeated label within a tensor");
+  for (int l : lc)
+    if (!has(la, l) && !has(lb, l)) return fail(TNQ_ERR_INVALID_ARG, "output label missing from both operands");
+  for (int l : la)
+    if (!has(lb, l) && !has(lc, l)) return fail(TNQ_ERR_INVALID_ARG, "label of A neither shared nor kept");
+  for (int l : lb)
+    if (!has(la, l) && !has(lc, l)) return fail(TNQ_ERR_INVALID_ARG, "label of B neither shared nor kept");
+  if (!ws || ws_bytes < contract_workspace_bytes(ctx->precision, ra, rb, rc))
+    return fail(TNQ_ERR_WORKSPACE, "workspace too small for tnq_contract_pair");
+  TNQ_CUDA(cudaSetDevice(ctx->device));
+  // A side = operand with fewer elements; K and H orders follow the other one
+  bool swap = ra > rb;
+  const std::vector<int>& xa = swap ? lb : la;
+  const std::vector<int>& xb = swap ? la : lb;
+  const void* pa = swap ? B : A;
+  const void* pb = swap ? A : B;
+  std::vector<int> K, Hh, M, N;
+  for (int l : xb)
+    if (has(xa, l)) (has(lc, l) ? Hh : K).push_back(l);
+  for (int l : xa)
+    if (!has(xb, l)) M.push_back(l);
+  for (int l : xb)
+    if (!has(xa, l)) N.push_back(l);
+  std::vector<int> a_req = K, b_req = K, out = N;
+  a_req.insert(a_req.end(), M.begin(), M.end());
+  a_req.insert(a_req.end(), Hh.begin(), Hh.end());
+  b_req.insert(b_req.end(), N.begin(), N.end());
+  b_req.insert(b_req.end(), Hh.begin(), Hh.end());
+  out.insert(out.end(), M.begin(), M.end());
+  out.insert(out.end(), Hh.begin(), Hh.end());
+  char* w = static_cast<char*>(ws);
+  size_t na = size_t(1) << std::max(ra, rb);
+  char* sa = w;
+  char* sb = w + ((32 * na + 4095) & ~size_t(4095));
+  char* sc = sb + ((16 * na + 4095) & ~size_t(4095));
+  bool direct = out == lc;
+  std::vector<int> none;
+  tnq_status st = run_gemm_step(ctx, pa, xa, xa != a_req, pb, xb, xb != b_req, a_req, b_req, none, 0,
+                                (int)Hh.size(), (int)M.size(), (int)N.size(), (int)K.size(), sa, sb,
+                                direct ? C : (void*)sc, nullptr);
+  if (st != TNQ_OK) return st;
+  if (!direct) {
+    PermDesc d;
+    build_perm_desc(out.data(), (int)out.size(), lc.data(), rc, nullptr, 0, PM_C64, 0, &d);
+    TNQ_CUDA(launch_permute(d, sc, C, nullptr, 0, ctx->sm_count, ctx->stream));
+  }
+  TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  return TNQ_OK;
+}
+
+}  // namespace tnq

@@ -1,0 +1,25 @@
+// Complex GEMM on the tcgen05 tensor cores (TMEM accumulators, TMA-staged
+// operands).  C[h][m][n] = sum_k A[h][m][k] B[h][n][k] computed as the real
+// product of the expansion A' (2M x 2K, rows (m,re|im), columns (k,re|im)) with
+// B (N rows of K interleaved complex values), FP32 accumulation.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace tnq {
+
+struct TcGemmArgs {
+  const void* a_hi = nullptr;  // A' (fp32 / tf32 / bf16 hi part), [batch][2M][2K]
+  const void* a_lo = nullptr;  // lo part (split modes) or null
+  const void* b_hi = nullptr;  // B, [batch][N][2K] reals
+  const void* b_lo = nullptr;
+  void* c = nullptr;           // complex64 [batch][M][N], or
+  void* acc = nullptr;         // complex128 accumulator (added to) when non-null
+  int M = 0, N = 0, K = 0, batch = 1;
+  int precision = 0;           // tnq_precision
+};
+
+// Returns cudaErrorNotSupported when the shape cannot run on the tensor cores.
+cudaError_t launch_cgemm_tc(const TcGemmArgs& g, int sm_count, cudaStream_t st);
+
+}  // namespace tnq

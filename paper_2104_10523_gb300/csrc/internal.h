@@ -1,0 +1,147 @@
+// Internal data structures of the tensor-network amplitude engine.
+//
+// Host side: circuit -> grouped network (Sec. 3.1, Fig. 1; one- and two-qubit
+// tensors merged as in Sec. 3.1.1, "small gate tensors are contracted
+// internally to form larger tensors") -> hypergraph -> contraction tree
+// (Sec. 3.1: FLOP minimisation by graph partitioning and heuristics) ->
+// sliced indices (Sec. 3.1) -> per-step GEMM layouts.
+// Device side: the executor runs every step as bit-permute + complex GEMM.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tnq.h"
+
+namespace tnq {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+tnq_status fail(tnq_status s, const std::string& msg);
+
+// ---------------------------------------------------------------- circuit
+struct COp {
+  bool channel = false;
+  std::vector<int> qubits;              // 1 or 2 qubits, qubits[0] = most significant
+  std::vector<std::vector<cd>> mats;    // gate: 1 matrix; channel: Kraus operators
+  std::vector<double> kraus_q;          // channel: q_k = Tr(A_k^dag A_k)/d
+  int channel_index = -1;               // channel: running index in circuit order
+};
+
+struct Circuit {
+  int n = 0;
+  std::vector<COp> ops;
+  int n_channels = 0;
+};
+
+// ---------------------------------------------------------------- network
+enum LeafKind { LEAF_STATIC = 0, LEAF_PROJ = 1, LEAF_TRAJ = 2 };
+
+// Product of a group of circuit ops acting on <= 2 qubits, as built on the GPU
+// per trajectory for LEAF_TRAJ leaves.
+struct GroupFactor {
+  int op;        // index into Circuit::ops
+  int slot_mask; // which group slots the op acts on: 1 = slot 0, 2 = slot 1, 3 = both
+  bool swap;     // two-qubit op listed as (slot1, slot0)
+};
+
+struct Leaf {
+  LeafKind kind = LEAF_STATIC;
+  std::vector<int> labels;        // storage order: labels[p] names bit p
+  std::vector<cd> data;           // LEAF_STATIC: 2^rank entries
+  int qubit = -1;                 // LEAF_PROJ: the projected qubit
+  // LEAF_TRAJ: operator on group slots, then legs fixed to |0>
+  int n_slots = 0;                // 1 or 2
+  std::vector<GroupFactor> factors;
+  int in_fixed_mask = 0;          // slot s input leg fixed to |0> when bit s set
+  int out_label[2] = {-1, -1};
+  int in_label[2] = {-1, -1};
+};
+
+struct Network {
+  int n_qubits = 0;
+  int n_labels = 0;
+  std::vector<Leaf> leaves;
+  std::vector<char> is_output;    // per label: kept to the end (batch labels)
+  std::vector<int> batch_labels;  // bit j of the bitstring index within a pass
+  std::vector<int> traj_labels;   // bit j of the trajectory index within a pass
+  bool noisy = false;
+};
+
+tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, Network* out);
+
+// ---------------------------------------------------------------- path search
+struct Tree {
+  int n_leaves = 0;
+  std::vector<std::pair<int, int>> nodes;  // internal node i has id n_leaves + i (post order)
+};
+
+struct TreeCost {
+  double flops = 0;      // one pass (one slice), 8 flops per complex MAC
+  double bytes = 0;      // algorithmic bytes of one pass
+  int max_log2 = 0;      // largest intermediate (log2 elements)
+};
+
+struct Hyper {
+  int n_labels = 0;
+  std::vector<std::vector<int>> leaf_labels;  // sorted
+  std::vector<char> is_output;
+  std::vector<int> label_count;
+};
+
+Hyper make_hyper(const Network& net);
+TreeCost tree_cost(const Hyper& h, const Tree& t, const std::vector<char>& sliced);
+Tree greedy_tree(const Hyper& h, const std::vector<char>& sliced, uint64_t seed, double temperature);
+Tree bisect_tree(const Hyper& h, uint64_t seed, double imbalance, int leaf_group);
+std::vector<int> choose_slices(const Hyper& h, const Tree& t, int cap_log2, bool* feasible);
+
+// ---------------------------------------------------------------- plan
+struct Step {
+  int a = -1, b = -1, out = -1;   // tensor ids (leaves 0..L-1, then step outputs)
+  int nH = 0, nM = 0, nN = 0, nK = 0;
+  std::vector<int> a_req, b_req;  // required operand layouts: [K][M|N][H] (bit 0 first)
+  std::vector<int> out_labels;    // [N][M][H]
+  bool perm_a = false, perm_b = false;
+  double flops = 0;
+};
+
+struct TensorSlot {
+  std::vector<int> labels;        // effective labels (sliced removed), storage order for outputs
+  int rank = 0;
+  size_t offset = 0;              // byte offset in workspace
+  bool leaf = false;
+};
+
+struct Plan {
+  Network net;
+  Hyper hyper;
+  Tree tree;
+  std::vector<char> sliced;       // per label
+  std::vector<int> slice_labels;  // bit j of the slice id = value of slice_labels[j]
+  std::vector<Step> steps;
+  std::vector<TensorSlot> tensors;
+  TreeCost cost;
+  double search_ms = 0;
+  int batch_log2 = 0, traj_log2 = 0;
+  int root = -1;
+  // workspace layout (bytes)
+  size_t ws_leaves = 0, ws_arena = 0, ws_arena_bytes = 0, ws_scratch_a = 0, ws_scratch_b = 0,
+         ws_scratch_bytes = 0, ws_acc = 0, ws_misc = 0, ws_total = 0;
+  int max_operand_log2 = 0;
+  // device binding
+  void* bound_ws = nullptr;
+  size_t bound_bytes = 0;
+  int bound_precision = -1;
+};
+
+tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p);
+void layout_steps(Plan* p);
+
+}  // namespace tnq
+
+struct tnq_circuit { tnq::Circuit c; };
+struct tnq_plan { tnq::Plan p; };

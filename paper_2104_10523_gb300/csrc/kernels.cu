@@ -1,0 +1,350 @@
+// Bit-permute, SIMT complex GEMM, projection fill and FP64 finalisation.
+//
+// Every index has dimension 2, so reordering a tensor's indices is a
+// permutation of the bits of its flat element index.  The permute kernel
+// stages tiles through shared memory: a tile spans the lowest destination bits
+// and the lowest source bits, so both the HBM read and the HBM write run along
+// contiguous runs.  It also writes the operand formats the GEMMs want (the real
+// expansion of a complex operand, TF32/BF16 hi-lo splits), so a step makes one
+// pass over each operand.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace tnq {
+
+// ------------------------------------------------------------------ permute
+void build_perm_desc(const int* src_labels, int src_rank, const int* dst_labels, int dst_rank,
+                     const int* slice_labels, int n_slice, int mode, int kbits, PermDesc* d) {
+  std::memset(d, 0, sizeof(*d));
+  d->r = dst_rank;
+  d->mode = mode;
+  d->kbits = kbits;
+  d->n_slice = n_slice;
+  auto src_pos = [&](int l) {
+    for (int p = 0; p < src_rank; ++p)
+      if (src_labels[p] == l) return p;
+    return -1;
+  };
+  std::vector<int> s_of_d(dst_rank);
+  for (int p = 0; p < dst_rank; ++p) s_of_d[p] = src_pos(dst_labels[p]);
+  for (int j = 0; j < n_slice; ++j) d->slice_src[j] = src_pos(slice_labels[j]);
+  for (int j = n_slice; j < 32; ++j) d->slice_src[j] = -1;
+  // tile: lowest destination bits and lowest source bits, grown until 10 bits
+  int target = std::min(dst_rank, 10);
+  std::vector<char> in_tile(dst_rank, 0);
+  int u = 0, a = 0, b = 0;
+  std::vector<int> d_of_s(src_rank, -1);
+  for (int p = 0; p < dst_rank; ++p) d_of_s[s_of_d[p]] = p;
+  while (u < target) {
+    if (a < dst_rank && (a <= b || b >= src_rank)) {
+      if (!in_tile[a]) {
+        in_tile[a] = 1;
+        ++u;
+      }
+      ++a;
+    } else if (b < src_rank) {
+      int p = d_of_s[b];
+      if (p >= 0 && !in_tile[p] && u < target) {
+        in_tile[p] = 1;
+        ++u;
+      }
+      ++b;
+    } else {
+      break;
+    }
+  }
+  d->u = u;
+  // tile bits in source order
+  std::vector<int> tile_dst;  // destination positions of tile bits, in source order
+  for (int s = 0; s < src_rank; ++s) {
+    int p = d_of_s[s];
+    if (p >= 0 && in_tile[p]) tile_dst.push_back(p);
+  }
+  for (int i = 0; i < u; ++i) d->tile_src[i] = s_of_d[tile_dst[i]];
+  std::vector<int> sorted = tile_dst;
+  std::sort(sorted.begin(), sorted.end());
+  for (int j = 0; j < u; ++j) {
+    d->tile_dst_sorted[j] = sorted[j];
+    d->tile_srcidx_of_dst[j] =
+        int(std::find(tile_dst.begin(), tile_dst.end(), sorted[j]) - tile_dst.begin());
+  }
+  int k = 0;
+  for (int p = 0; p < dst_rank; ++p)
+    if (!in_tile[p]) {
+      d->outer_dst[k] = p;
+      d->outer_src[k] = s_of_d[p];
+      ++k;
+    }
+  d->n_outer = k;
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void write_operand(const PermDesc& d, void* dst0, void* dst1, size_t o,
+                                              float2 v) {
+  switch (d.mode) {
+    case PM_C64:
+      reinterpret_cast<float2*>(dst0)[o] = v;
+      break;
+    case PM_AEXP_F32:
+    case PM_AEXP_TF32:
+    case PM_AEXP_TF32X3:
+    case PM_AEXP_BF16X3: {
+      size_t K = size_t(1) << d.kbits;
+      size_t row = o >> d.kbits, k = o & (K - 1);
+      size_t i0 = (2 * row) * K + k, i1 = (2 * row + 1) * K + k;
+      float re = v.x, im = v.y;
+      if (d.mode == PM_AEXP_F32) {
+        reinterpret_cast<float2*>(dst0)[i0] = make_float2(re, -im);
+        reinterpret_cast<float2*>(dst0)[i1] = make_float2(im, re);
+      } else if (d.mode == PM_AEXP_TF32) {
+        float hr = tf32_round(re), hi = tf32_round(im);
+        reinterpret_cast<float2*>(dst0)[i0] = make_float2(hr, -hi);
+        reinterpret_cast<float2*>(dst0)[i1] = make_float2(hi, hr);
+      } else if (d.mode == PM_AEXP_TF32X3) {
+        float hr = tf32_round(re), hi = tf32_round(im);
+        float lr = tf32_round(re - hr), li = tf32_round(im - hi);
+        reinterpret_cast<float2*>(dst0)[i0] = make_float2(hr, -hi);
+        reinterpret_cast<float2*>(dst0)[i1] = make_float2(hi, hr);
+        reinterpret_cast<float2*>(dst1)[i0] = make_float2(lr, -li);
+        reinterpret_cast<float2*>(dst1)[i1] = make_float2(li, lr);
+      } else {
+        __nv_bfloat16 hr = __float2bfloat16_rn(re), hi = __float2bfloat16_rn(im);
+        __nv_bfloat16 lr = __float2bfloat16_rn(re - __bfloat162float(hr));
+        __nv_bfloat16 li = __float2bfloat16_rn(im - __bfloat162float(hi));
+        __nv_bfloat162 h0, h1, l0, l1;
+        h0.x = hr; h0.y = __hneg(hi);
+        h1.x = hi; h1.y = hr;
+        l0.x = lr; l0.y = __hneg(li);
+        l1.x = li; l1.y = lr;
+        reinterpret_cast<__nv_bfloat162*>(dst0)[i0] = h0;
+        reinterpret_cast<__nv_bfloat162*>(dst0)[i1] = h1;
+        reinterpret_cast<__nv_bfloat162*>(dst1)[i0] = l0;
+        reinterpret_cast<__nv_bfloat162*>(dst1)[i1] = l1;
+      }
+      break;
+    }
+    case PM_B_TF32:
+      reinterpret_cast<float2*>(dst0)[o] = make_float2(tf32_round(v.x), tf32_round(v.y));
+      break;
+    case PM_B_TF32X3: {
+      float hr = tf32_round(v.x), hi = tf32_round(v.y);
+      reinterpret_cast<float2*>(dst0)[o] = make_float2(hr, hi);
+      reinterpret_cast<float2*>(dst1)[o] = make_float2(tf32_round(v.x - hr), tf32_round(v.y - hi));
+      break;
+    }
+    case PM_B_BF16X3: {
+      __nv_bfloat162 h, l;
+      h.x = __float2bfloat16_rn(v.x);
+      h.y = __float2bfloat16_rn(v.y);
+      l.x = __float2bfloat16_rn(v.x - __bfloat162float(h.x));
+      l.y = __float2bfloat16_rn(v.y - __bfloat162float(h.y));
+      reinterpret_cast<__nv_bfloat162*>(dst0)[o] = h;
+      reinterpret_cast<__nv_bfloat162*>(dst1)[o] = l;
+      break;
+    }
+  }
+}
+
+constexpr int PERM_THREADS = 256;
+
+__global__ void __launch_bounds__(PERM_THREADS) permute_kernel(const PermDesc d, const float2* __restrict__ src,
+                                                               void* dst0, void* dst1, int slice_id) {
+  __shared__ float2 tile[1024];
+  __shared__ uint32_t srcoff[1024];
+  __shared__ uint32_t dstoff[1024];
+  __shared__ uint16_t eidx[1024];
+  const int T = 1 << d.u;
+  for (int e = threadIdx.x; e < T; e += blockDim.x) {
+    uint32_t s = 0, o = 0, ei = 0;
+    for (int i = 0; i < d.u; ++i)
+      if ((e >> i) & 1) {
+        s |= 1u << d.tile_src[i];
+        o |= 1u << d.tile_dst_sorted[i];
+        ei |= 1u << d.tile_srcidx_of_dst[i];
+      }
+    srcoff[e] = s;
+    dstoff[e] = o;
+    eidx[e] = (uint16_t)ei;
+  }
+  size_t slice_off = 0;
+  for (int j = 0; j < d.n_slice; ++j)
+    if (d.slice_src[j] >= 0 && ((slice_id >> j) & 1)) slice_off |= size_t(1) << d.slice_src[j];
+  __syncthreads();
+  const size_t n_outer = size_t(1) << d.n_outer;
+  for (size_t c = blockIdx.x; c < n_outer; c += gridDim.x) {
+    size_t sb = slice_off, db = 0;
+    for (int k = 0; k < d.n_outer; ++k)
+      if ((c >> k) & 1) {
+        sb |= size_t(1) << d.outer_src[k];
+        db |= size_t(1) << d.outer_dst[k];
+      }
+    for (int e = threadIdx.x; e < T; e += blockDim.x) tile[e] = src[sb + srcoff[e]];
+    __syncthreads();
+    for (int f = threadIdx.x; f < T; f += blockDim.x) write_operand(d, dst0, dst1, db + dstoff[f], tile[eidx[f]]);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_permute(const PermDesc& d, const void* src, void* dst0, void* dst1, int slice_id,
+                           int sm_count, cudaStream_t st) {
+  size_t n_outer = size_t(1) << d.n_outer;
+  size_t grid = std::min<size_t>(n_outer, size_t(sm_count) * 8);
+  permute_kernel<<<(unsigned)grid, PERM_THREADS, 0, st>>>(d, reinterpret_cast<const float2*>(src), dst0,
+                                                          dst1, slice_id);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ SIMT complex GEMM
+// 64x64 complex tile per CTA, 16-deep K slices in shared memory, 4x4 complex
+// outputs per thread (strided so that shared-memory reads and global stores are
+// conflict-free and coalesced).
+constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16;
+
+__global__ void __launch_bounds__(256) cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                         float2* __restrict__ C, double2* __restrict__ acc, int M,
+                                                         int N, int K, int batch) {
+  __shared__ float2 As[SG_BK][SG_BM + 1];
+  __shared__ float2 Bs[SG_BK][SG_BN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tiles_n = (N + SG_BN - 1) / SG_BN;
+  const int n0 = int(blockIdx.x % tiles_n) * SG_BN, m0 = int(blockIdx.x / tiles_n) * SG_BM;
+  for (int h = blockIdx.z; h < batch; h += gridDim.z) {
+    const float2* Ah = A + size_t(h) * M * K;
+    const float2* Bh = B + size_t(h) * N * K;
+    float cr[4][4], ci[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cr[i][j] = ci[i][j] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += SG_BK) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        int idx = tid + 256 * l, r = idx >> 4, kk = idx & 15;
+        float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+        if (m0 + r < M && k0 + kk < K) va = Ah[size_t(m0 + r) * K + k0 + kk];
+        if (n0 + r < N && k0 + kk < K) vb = Bh[size_t(n0 + r) * K + k0 + kk];
+        As[kk][r] = va;
+        Bs[kk][r] = vb;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < SG_BK; ++kk) {
+        float2 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
+            cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
+            ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
+            ci[i][j] = fmaf(a[i].y, b[j].x, ci[i][j]);
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+        if (m < M && n < N) {
+          size_t o = size_t(h) * M * N + size_t(m) * N + n;
+          if (acc) {
+            double2 t = acc[o];
+            t.x += (double)cr[i][j];
+            t.y += (double)ci[i][j];
+            acc[o] = t;
+          } else {
+            C[o] = make_float2(cr[i][j], ci[i][j]);
+          }
+        }
+      }
+  }
+}
+
+cudaError_t launch_cgemm_simt(const void* A, const void* B, void* C, void* acc, int M, int N, int K,
+                              int batch, cudaStream_t st) {
+  size_t tiles = size_t((N + SG_BN - 1) / SG_BN) * size_t((M + SG_BM - 1) / SG_BM);
+  if (tiles > 0x7fffffffu) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)tiles, 1, std::min(batch, 65535));
+  cgemm_simt_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(B),
+                                          reinterpret_cast<float2*>(C), reinterpret_cast<double2*>(acc), M, N,
+                                          K, batch);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ projection fill
+__global__ void proj_fill_kernel(char* base, size_t stride, int n, int w, const int8_t* __restrict__ bits,
+                                 int64_t n_valid, int* err) {
+  const int64_t per = int64_t(1) << w;
+  const int64_t total = per * n;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    int q = int(t / per);
+    int64_t b = t % per;
+    float2* P = reinterpret_cast<float2*>(base + stride * q);
+    float v0 = 0.f, v1 = 0.f;
+    if (b < n_valid) {
+      int8_t x = bits[b * n + q];
+      if (x == 0) v0 = 1.f;
+      else if (x == 1) v1 = 1.f;
+      else atomicOr(err, 1);
+    }
+    P[2 * b] = make_float2(v0, 0.f);
+    P[2 * b + 1] = make_float2(v1, 0.f);
+  }
+}
+
+cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_qubits, int batch_log2,
+                             const int8_t* bits, int64_t n_valid, int* err_flag, cudaStream_t st) {
+  int64_t total = (int64_t(1) << batch_log2) * n_qubits;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  proj_fill_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<char*>(leaves_base), stride_bytes, n_qubits,
+                                           batch_log2, bits, n_valid, err_flag);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ finalize
+struct PosTable {
+  int n;
+  int pos[32];
+};
+
+__global__ void finalize_kernel(const double2* __restrict__ acc, double2* __restrict__ out, int64_t n_valid,
+                                PosTable pt) {
+  for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < n_valid; b += int64_t(gridDim.x) * blockDim.x) {
+    size_t r = 0;
+    for (int j = 0; j < pt.n; ++j)
+      if ((b >> j) & 1) r |= size_t(1) << pt.pos[j];
+    out[b] = acc[r];
+  }
+}
+
+cudaError_t launch_finalize(const void* acc, void* out, int64_t n_valid, const int* pos_table, int n_pos,
+                            cudaStream_t st) {
+  PosTable pt;
+  pt.n = n_pos;
+  for (int j = 0; j < n_pos && j < 32; ++j) pt.pos[j] = pos_table[j];
+  int blocks = (int)std::min<int64_t>((n_valid + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  finalize_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(acc), reinterpret_cast<double2*>(out),
+                                          n_valid, pt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
+
+}  // namespace tnq

@@ -1,0 +1,59 @@
+// Device kernels and their launch descriptors (shared by the executor and the
+// pairwise-contraction entry point).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tnq {
+
+// Operand formats written by the permute kernel.
+enum PermMode {
+  PM_C64 = 0,          // complex64 copy in the new order
+  PM_AEXP_F32 = 1,     // A' = [[re,-im],[im,re]] real expansion, FP32 (2 rows x 2K floats per complex row)
+  PM_AEXP_TF32 = 2,    // as above, rounded to TF32
+  PM_AEXP_TF32X3 = 3,  // as above, hi/lo TF32 split into dst0/dst1
+  PM_AEXP_BF16X3 = 4,  // as above, hi/lo BF16 split
+  PM_B_TF32 = 5,       // complex64 rounded to TF32
+  PM_B_TF32X3 = 6,     // complex64 hi/lo TF32 split
+  PM_B_BF16X3 = 7      // complex pairs as bf16x2, hi/lo split
+};
+
+struct PermDesc {
+  int r;                       // destination rank
+  int u;                       // bits staged per tile
+  int n_outer;                 // r - u
+  int kbits;                   // A' expansion: number of K bits (lowest destination bits)
+  int mode;
+  int n_slice;                 // slice-id bits
+  int tile_src[16];            // i-th tile bit (source order): its source bit position
+  int tile_dst_sorted[16];     // tile bits in destination order: destination bit position
+  int tile_srcidx_of_dst[16];  // j-th tile bit in destination order -> its source-order index
+  int outer_src[32];
+  int outer_dst[32];
+  int slice_src[32];           // source bit of slice bit j, or -1
+};
+
+void build_perm_desc(const int* src_labels, int src_rank, const int* dst_labels, int dst_rank,
+                     const int* slice_labels, int n_slice, int mode, int kbits, PermDesc* d);
+
+cudaError_t launch_permute(const PermDesc& d, const void* src, void* dst0, void* dst1, int slice_id,
+                           int sm_count, cudaStream_t st);
+
+// C[h][m][n] = sum_k A[h][m][k] * B[h][n][k] (complex64, FP32 FFMA); with acc
+// non-null the result is added in FP64 to acc (same layout) instead of stored.
+cudaError_t launch_cgemm_simt(const void* A, const void* B, void* C, void* acc, int M, int N, int K,
+                              int batch, cudaStream_t st);
+
+// Projection leaves: P_q[(b << 1) | x] = [bits[(base+b)*n + q] == x] for b < n_valid, else 0.
+cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_qubits, int batch_log2,
+                             const int8_t* bits, int64_t n_valid, int* err_flag, cudaStream_t st);
+
+// out[b] = acc[root_index(b)] for b < n_valid (complex128), where
+// root_index(b) = sum_j bit_j(b) << pos[j].
+cudaError_t launch_finalize(const void* acc, void* out, int64_t n_valid, const int* pos_table,
+                            int n_pos, cudaStream_t st);
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+}  // namespace tnq

@@ -1,0 +1,224 @@
+// Plan = network + contraction tree + sliced labels + per-step GEMM layouts +
+// workspace layout.  Host only.
+//
+// Each internal tree node is one pairwise contraction (Sec. 3.1).  Its labels
+// split into H (batch: held by both operands and kept), K (contracted), M
+// (operand A only), N (operand B only).  The step runs as a batched complex
+// GEMM C[h][m][n] = sum_k A[h][m][k] B[h][n][k]; operands whose stored label
+// order differs from [K][M|N][H] (bit 0 first) are bit-permuted first, and the
+// output is stored as [N][M][H] so that the next step often needs no permute.
+// Sliced labels are fixed per pass (Sec. 3.1 slicing); only leaves hold them,
+// and a leaf holding one is always gathered through the permute kernel.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <random>
+
+#include "internal.h"
+
+namespace tnq {
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool contains(const std::vector<int>& v, int l) { return std::find(v.begin(), v.end(), l) != v.end(); }
+
+}  // namespace
+
+void layout_steps(Plan* p) {
+  const Hyper& h = p->hyper;
+  const Tree& t = p->tree;
+  const int L = t.n_leaves;
+  p->tensors.assign(L + t.nodes.size(), TensorSlot());
+  for (int i = 0; i < L; ++i) {
+    auto& ts = p->tensors[i];
+    ts.leaf = true;
+    ts.labels = p->net.leaves[i].labels;  // storage order, may include sliced labels
+    ts.rank = (int)ts.labels.size();
+  }
+  // subtree label counts for open/closed decisions
+  std::vector<std::map<int, int>> cnt(L + t.nodes.size());
+  for (int i = 0; i < L; ++i)
+    for (int l : p->net.leaves[i].labels)
+      if (!p->sliced[l]) cnt[i][l] = 1;
+  auto eff = [&](int id) {
+    std::vector<int> v;
+    for (int l : p->tensors[id].labels)
+      if (!p->sliced[l]) v.push_back(l);
+    return v;
+  };
+  p->steps.clear();
+  int max_op = 0;
+  for (int j = 0; j < (int)t.nodes.size(); ++j) {
+    int x = t.nodes[j].first, y = t.nodes[j].second, id = L + j;
+    for (auto& e : cnt[x]) cnt[id][e.first] += e.second;
+    for (auto& e : cnt[y]) cnt[id][e.first] += e.second;
+    std::vector<int> out_set;
+    for (auto& e : cnt[id])
+      if (h.is_output[e.first] || e.second < h.label_count[e.first]) out_set.push_back(e.first);
+    std::vector<int> lx = eff(x), ly = eff(y);
+    // A = operand with fewer elements (it is the one expanded for the tensor cores)
+    bool x_is_a = lx.size() <= ly.size();
+    int a = x_is_a ? x : y, b = x_is_a ? y : x;
+    std::vector<int> la = x_is_a ? lx : ly, lb = x_is_a ? ly : lx;
+    const std::vector<int>& anchor = lb;  // K and H orders follow the larger operand
+    std::vector<int> K, Hh, M, N;
+    for (int l : anchor)
+      if (contains(la, l)) (contains(out_set, l) ? Hh : K).push_back(l);
+    for (int l : la)
+      if (!contains(lb, l)) M.push_back(l);
+    for (int l : lb)
+      if (!contains(la, l)) N.push_back(l);
+    Step s;
+    s.a = a;
+    s.b = b;
+    s.out = id;
+    s.nH = (int)Hh.size();
+    s.nM = (int)M.size();
+    s.nN = (int)N.size();
+    s.nK = (int)K.size();
+    s.a_req = K;
+    s.a_req.insert(s.a_req.end(), M.begin(), M.end());
+    s.a_req.insert(s.a_req.end(), Hh.begin(), Hh.end());
+    s.b_req = K;
+    s.b_req.insert(s.b_req.end(), N.begin(), N.end());
+    s.b_req.insert(s.b_req.end(), Hh.begin(), Hh.end());
+    s.out_labels = N;
+    s.out_labels.insert(s.out_labels.end(), M.begin(), M.end());
+    s.out_labels.insert(s.out_labels.end(), Hh.begin(), Hh.end());
+    s.perm_a = p->tensors[a].labels != s.a_req;
+    s.perm_b = p->tensors[b].labels != s.b_req;
+    s.flops = 8.0 * std::ldexp(1.0, s.nH + s.nM + s.nN + s.nK);
+    auto& ts = p->tensors[id];
+    ts.labels = s.out_labels;
+    ts.rank = (int)s.out_labels.size();
+    max_op = std::max({max_op, (int)s.a_req.size(), (int)s.b_req.size()});
+    p->steps.push_back(s);
+    cnt[x].clear();
+    cnt[y].clear();
+  }
+  p->root = L + (int)t.nodes.size() - 1;
+  p->max_operand_log2 = max_op;
+
+  // ---- workspace: [leaves][arena of intermediates][scratch A][scratch B][acc][misc]
+  size_t off = 0;
+  for (int i = 0; i < L; ++i) {
+    off = align_up(off, 256);
+    p->tensors[i].offset = off;
+    off += (size_t(8) << p->tensors[i].rank);
+  }
+  p->ws_leaves = 0;
+  size_t arena_base = align_up(off, 256);
+  // first-fit arena over step outputs with liveness (an output lives until the
+  // step that consumes it; the root lives to the end)
+  struct Blk {
+    size_t off, size;
+    int owner;
+  };
+  std::vector<Blk> live;
+  size_t arena_top = 0;
+  auto alloc = [&](size_t sz, int owner) {
+    sz = align_up(sz, 256);
+    std::sort(live.begin(), live.end(), [](const Blk& u, const Blk& v) { return u.off < v.off; });
+    size_t cur = 0;
+    for (auto& bk : live) {
+      if (bk.off >= cur + sz) break;
+      cur = std::max(cur, bk.off + bk.size);
+    }
+    live.push_back({cur, sz, owner});
+    arena_top = std::max(arena_top, cur + sz);
+    return cur;
+  };
+  auto release = [&](int owner) {
+    live.erase(std::remove_if(live.begin(), live.end(), [&](const Blk& bk) { return bk.owner == owner; }),
+               live.end());
+  };
+  for (auto& s : p->steps) {
+    p->tensors[s.out].offset = arena_base + alloc(size_t(8) << p->tensors[s.out].rank, s.out);
+    if (s.a >= L) release(s.a);
+    if (s.b >= L) release(s.b);
+  }
+  p->ws_arena = arena_base;
+  p->ws_arena_bytes = arena_top;
+  off = align_up(arena_base + arena_top, 1024);
+  // scratch: A expanded to 2Mx2K reals with a hi/lo split (32 B per complex
+  // element, worst case), B with a hi/lo split (16 B per complex element)
+  size_t max_a = 0, max_b = 0;
+  for (auto& s : p->steps) {
+    max_a = std::max(max_a, size_t(1) << s.a_req.size());
+    max_b = std::max(max_b, size_t(1) << s.b_req.size());
+  }
+  p->ws_scratch_a = off;
+  off = align_up(off + 32 * max_a + 4096, 1024);
+  p->ws_scratch_b = off;
+  off = align_up(off + 16 * max_b + 4096, 1024);
+  p->ws_scratch_bytes = 32 * max_a + 16 * max_b;
+  p->ws_acc = off;
+  off = align_up(off + 16 * (size_t(1) << p->tensors[p->root].rank), 256);
+  p->ws_misc = off;
+  size_t nbits = size_t(p->net.n_qubits) << p->batch_log2;
+  off = align_up(off + 256 + align_up(nbits, 256) + 16 * (size_t(1) << p->batch_log2), 256);
+  p->ws_total = off;
+}
+
+tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (o.batch_log2 < 0 || o.batch_log2 > 16 || o.traj_log2 < 0 || o.traj_log2 > 16)
+    return fail(TNQ_ERR_INVALID_ARG, "batch_log2/traj_log2 must be in [0, 16]");
+  if (o.max_intermediate_log2 < 1 || o.max_intermediate_log2 > 31)
+    return fail(TNQ_ERR_INVALID_ARG, "max_intermediate_log2 must be in [1, 31]");
+  p->batch_log2 = o.batch_log2;
+  p->traj_log2 = c.n_channels > 0 ? o.traj_log2 : 0;
+  tnq_status st = build_network(c, p->batch_log2, p->traj_log2, &p->net);
+  if (st != TNQ_OK) return st;
+  p->hyper = make_hyper(p->net);
+  const Hyper& h = p->hyper;
+  std::vector<Tree> cands;
+  int mode = o.path_mode;
+  int nc = std::max(1, o.n_candidates);
+  if (mode == TNQ_PATH_GREEDY || mode == TNQ_PATH_BEST || mode == TNQ_PATH_LEARNED)
+    cands.push_back(greedy_tree(h, {}, o.seed, 0.0));
+  if (mode == TNQ_PATH_BISECT || mode == TNQ_PATH_BEST || mode == TNQ_PATH_LEARNED) {
+    std::mt19937_64 g(o.seed ^ 0x5bd1e995ULL);
+    for (int i = 0; i < nc; ++i) {
+      double imb = 0.05 + 0.6 * ((g() >> 11) * (1.0 / 9007199254740992.0));
+      int grp = 4 + int(g() % 12);
+      cands.push_back(bisect_tree(h, g(), imb, grp));
+    }
+    for (int i = 0; i < nc / 4; ++i) cands.push_back(greedy_tree(h, {}, g(), 0.3 + 0.2 * (i % 4)));
+  }
+  if (cands.empty()) return fail(TNQ_ERR_INVALID_ARG, "unknown path_mode");
+  double best_total = 0;
+  int best = -1;
+  std::vector<int> best_slices;
+  for (int i = 0; i < (int)cands.size(); ++i) {
+    bool feas = false;
+    std::vector<int> sl = choose_slices(h, cands[i], o.max_intermediate_log2, &feas);
+    if (!feas) continue;
+    std::vector<char> sv(h.n_labels, 0);
+    for (int l : sl) sv[l] = 1;
+    TreeCost tc = tree_cost(h, cands[i], sv);
+    double total = tc.flops * std::ldexp(1.0, (int)sl.size());
+    if (best < 0 || total < best_total) {
+      best = i;
+      best_total = total;
+      best_slices = sl;
+    }
+  }
+  if (best < 0)
+    return fail(TNQ_ERR_PLAN_INFEASIBLE,
+                "no contraction tree and slicing keeps every intermediate within 2^" +
+                    std::to_string(o.max_intermediate_log2) + " elements");
+  p->tree = cands[best];
+  p->sliced.assign(h.n_labels, 0);
+  p->slice_labels = best_slices;
+  for (int l : best_slices) p->sliced[l] = 1;
+  p->cost = tree_cost(h, p->tree, p->sliced);
+  layout_steps(p);
+  p->search_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return TNQ_OK;
+}
+
+}  // namespace tnq

@@ -1,0 +1,289 @@
+"""ctypes binding of libtnq (include/tnq.h): same names, argument marshalling only.
+
+Every step of the contraction runs inside libtnq's own CUDA kernels; this
+module only converts Python/NumPy/torch arguments to the C ABI.  Loading fails
+loudly when the library has not been built (``paper_2104_10523_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TNQ_OK = 0
+TNQ_ERR_INVALID_ARG = 1
+TNQ_ERR_PLAN_INFEASIBLE = 2
+TNQ_ERR_WORKSPACE = 3
+TNQ_ERR_CUDA = 4
+TNQ_ERR_TIMEOUT = 5
+TNQ_ERR_NOT_SUPPORTED = 6
+TNQ_ERR_NO_DEVICE = 7
+
+TNQ_PREC_FP32, TNQ_PREC_TF32, TNQ_PREC_TF32X3, TNQ_PREC_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3}
+TNQ_PATH_GREEDY, TNQ_PATH_BISECT, TNQ_PATH_BEST, TNQ_PATH_LEARNED = 0, 1, 2, 3
+
+# Every exported symbol of include/tnq.h (checked by the CPU tests).
+EXPORTS = (
+    "tnq_version", "tnq_status_string", "tnq_last_error",
+    "tnq_circuit_create", "tnq_circuit_destroy", "tnq_circuit_gate", "tnq_circuit_channel",
+    "tnq_circuit_n_qubits", "tnq_plan_create", "tnq_plan_destroy", "tnq_plan_get_info",
+    "tnq_plan_get_steps", "tnq_ctx_create", "tnq_ctx_destroy", "tnq_ctx_set_precision",
+    "tnq_plan_bind", "tnq_amplitudes", "tnq_noisy_probabilities",
+    "tnq_contract_workspace_bytes", "tnq_contract_pair",
+)
+
+
+class TnqOptions(C.Structure):
+    _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("precision", C.c_int)]
+
+
+class TnqPlanOpts(C.Structure):
+    _fields_ = [("max_intermediate_log2", C.c_int), ("batch_log2", C.c_int), ("traj_log2", C.c_int),
+                ("path_mode", C.c_int), ("n_candidates", C.c_int), ("seed", C.c_uint64)]
+
+
+class TnqPlanInfo(C.Structure):
+    _fields_ = [("n_leaves", C.c_int), ("n_steps", C.c_int), ("n_sliced", C.c_int), ("max_log2", C.c_int),
+                ("batch_log2", C.c_int), ("traj_log2", C.c_int), ("flops_per_pass", C.c_double),
+                ("flops_per_batch", C.c_double), ("bytes_per_pass", C.c_double), ("search_ms", C.c_double),
+                ("workspace_bytes", C.c_size_t)]
+
+
+class TnqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"tnq status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtnq is not built ({path} missing); run paper_2104_10523_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, ip, i32, i64, u64, dp, sz = C.c_void_p, C.POINTER(C.c_int), C.c_int, C.c_int64, C.c_uint64, \
+        C.POINTER(C.c_double), C.c_size_t
+    sig = {
+        "tnq_version": ([], C.c_char_p),
+        "tnq_status_string": ([i32], C.c_char_p),
+        "tnq_last_error": ([], C.c_char_p),
+        "tnq_circuit_create": ([i32, C.POINTER(vp)], i32),
+        "tnq_circuit_destroy": ([vp], None),
+        "tnq_circuit_gate": ([vp, i32, ip, dp], i32),
+        "tnq_circuit_channel": ([vp, i32, ip, i32, dp], i32),
+        "tnq_circuit_n_qubits": ([vp], i32),
+        "tnq_plan_create": ([vp, C.POINTER(TnqPlanOpts), C.POINTER(vp)], i32),
+        "tnq_plan_destroy": ([vp], None),
+        "tnq_plan_get_info": ([vp, C.POINTER(TnqPlanInfo)], i32),
+        "tnq_plan_get_steps": ([vp, ip], i32),
+        "tnq_ctx_create": ([C.POINTER(TnqOptions), C.POINTER(vp)], i32),
+        "tnq_ctx_destroy": ([vp], None),
+        "tnq_ctx_set_precision": ([vp, i32], i32),
+        "tnq_plan_bind": ([vp, vp, vp, sz], i32),
+        "tnq_amplitudes": ([vp, vp, i64, vp, vp], i32),
+        "tnq_noisy_probabilities": ([vp, vp, i64, u64, i64, vp, vp, vp], i32),
+        "tnq_contract_workspace_bytes": ([i32, i32, i32, i32], sz),
+        "tnq_contract_pair": ([vp, vp, i32, ip, vp, i32, ip, vp, i32, ip, vp, sz], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != TNQ_OK:
+        raise TnqError(status, load().tnq_last_error().decode())
+
+
+def _int_array(v):
+    return (C.c_int * len(v))(*[int(x) for x in v])
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or a NumPy array (host or device)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+# ---------------------------------------------------------------- thin wrappers
+def tnq_version() -> str:
+    return load().tnq_version().decode()
+
+
+def tnq_circuit_create(n_qubits: int):
+    h = C.c_void_p()
+    check(load().tnq_circuit_create(int(n_qubits), C.byref(h)))
+    return h
+
+
+def tnq_circuit_destroy(h):
+    load().tnq_circuit_destroy(h)
+
+
+def tnq_circuit_gate(h, qubits, matrix):
+    m = np.ascontiguousarray(np.asarray(matrix, np.complex128)).view(np.float64)
+    check(load().tnq_circuit_gate(h, len(qubits), _int_array(qubits),
+                                  m.ctypes.data_as(C.POINTER(C.c_double))))
+
+
+def tnq_circuit_channel(h, qubits, kraus):
+    k = np.ascontiguousarray(np.asarray(kraus, np.complex128)).view(np.float64)
+    check(load().tnq_circuit_channel(h, len(qubits), _int_array(qubits), len(kraus),
+                                     k.ctypes.data_as(C.POINTER(C.c_double))))
+
+
+def tnq_plan_create(circ_h, max_intermediate_log2=28, batch_log2=0, traj_log2=0,
+                    path_mode=TNQ_PATH_BEST, n_candidates=16, seed=0):
+    o = TnqPlanOpts(max_intermediate_log2, batch_log2, traj_log2, path_mode, n_candidates, seed)
+    h = C.c_void_p()
+    check(load().tnq_plan_create(circ_h, C.byref(o), C.byref(h)))
+    return h
+
+
+def tnq_plan_destroy(h):
+    load().tnq_plan_destroy(h)
+
+
+def tnq_plan_get_info(h) -> dict:
+    info = TnqPlanInfo()
+    check(load().tnq_plan_get_info(h, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in TnqPlanInfo._fields_}
+
+
+def tnq_plan_get_steps(h, n_steps) -> np.ndarray:
+    rec = np.zeros(8 * n_steps, dtype=np.int32)
+    check(load().tnq_plan_get_steps(h, rec.ctypes.data_as(C.POINTER(C.c_int))))
+    return rec.reshape(n_steps, 8)
+
+
+def tnq_ctx_create(device=0, stream=None, precision=TNQ_PREC_FP32):
+    o = TnqOptions(int(device), C.c_void_p(stream or 0), int(precision))
+    h = C.c_void_p()
+    check(load().tnq_ctx_create(C.byref(o), C.byref(h)))
+    return h
+
+
+def tnq_ctx_destroy(h):
+    load().tnq_ctx_destroy(h)
+
+
+def tnq_ctx_set_precision(h, precision):
+    check(load().tnq_ctx_set_precision(h, int(precision)))
+
+
+def tnq_plan_bind(ctx, plan, workspace, nbytes):
+    check(load().tnq_plan_bind(ctx, plan, _ptr(workspace), int(nbytes)))
+
+
+def tnq_amplitudes(ctx, plan, bits, out):
+    """bits: int8 [n_bs][n] (NumPy host or torch device); out: float64 [n_bs][2] (same choices)."""
+    n_bs = int(bits.shape[0])
+    check(load().tnq_amplitudes(ctx, plan, n_bs, _ptr(bits), _ptr(out)))
+
+
+def tnq_noisy_probabilities(ctx, plan, n_traj, seed, bits, p_out, se_out=None):
+    check(load().tnq_noisy_probabilities(ctx, plan, int(n_traj), int(seed), int(bits.shape[0]), _ptr(bits),
+                                         _ptr(p_out), _ptr(se_out)))
+
+
+def tnq_contract_workspace_bytes(precision, ra, rb, rc) -> int:
+    return int(load().tnq_contract_workspace_bytes(int(precision), int(ra), int(rb), int(rc)))
+
+
+def tnq_contract_pair(ctx, A, a_labels, B, b_labels, Cout, c_labels, workspace, nbytes):
+    check(load().tnq_contract_pair(ctx, _ptr(A), len(a_labels), _int_array(a_labels), _ptr(B), len(b_labels),
+                                   _int_array(b_labels), _ptr(Cout), len(c_labels), _int_array(c_labels),
+                                   _ptr(workspace), int(nbytes)))
+
+
+# ---------------------------------------------------------------- owning helpers
+class Circuit:
+    """Owns a tnq_circuit built from a workloads.Circuit (gates and channels in order)."""
+
+    def __init__(self, circ):
+        self.n = circ.n
+        self.h = tnq_circuit_create(circ.n)
+        for op in circ.ops:
+            if op.kind == "gate":
+                tnq_circuit_gate(self.h, op.qubits, op.mats[0])
+            else:
+                tnq_circuit_channel(self.h, op.qubits, np.stack(op.mats))
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.tnq_circuit_destroy(self.h)
+            self.h = None
+
+
+class Plan:
+    """Owns a tnq_plan; info() and steps() describe it."""
+
+    def __init__(self, circuit: Circuit, **opts):
+        self.circuit = circuit
+        self.h = tnq_plan_create(circuit.h, **opts)
+        self.info = tnq_plan_get_info(self.h)
+        self.workspace = None
+
+    def steps(self):
+        return tnq_plan_get_steps(self.h, self.info["n_steps"])
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.tnq_plan_destroy(self.h)
+            self.h = None
+
+
+class Context:
+    """Owns a tnq_ctx on a device and the torch stream it orders work on."""
+
+    def __init__(self, device=0, precision="fp32", stream=None):
+        import torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.h = tnq_ctx_create(device, self.stream.cuda_stream, prec)
+
+    def set_precision(self, precision):
+        tnq_ctx_set_precision(self.h, PRECISIONS[precision] if isinstance(precision, str) else int(precision))
+
+    def bind(self, plan: Plan):
+        import torch
+        nbytes = int(plan.info["workspace_bytes"])
+        plan.workspace = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+        tnq_plan_bind(self.h, plan.h, plan.workspace, nbytes)
+
+    def amplitudes(self, plan: Plan, bits):
+        """complex128 amplitudes; bits: int8 NumPy [n_bs][n] (host) or a torch cuda int8 tensor."""
+        if hasattr(bits, "is_cuda") and bits.is_cuda:
+            import torch
+            out = torch.empty((bits.shape[0], 2), dtype=torch.float64, device=bits.device)
+            tnq_amplitudes(self.h, plan.h, bits, out)
+            return out
+        b = np.ascontiguousarray(bits, dtype=np.int8)
+        out = np.empty((b.shape[0], 2), dtype=np.float64)
+        tnq_amplitudes(self.h, plan.h, b, out)
+        return out[:, 0] + 1j * out[:, 1]
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.tnq_ctx_destroy(self.h)
+            self.h = None

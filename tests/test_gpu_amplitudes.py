@@ -1,0 +1,142 @@
+"""GPU parity of the amplitude path against the FP64 CPU oracle.
+
+Tolerance: relative L2 error over the batch, ||a_gpu - a_ref|| / ||a_ref||
+(per-amplitude relative error is ill-conditioned for tiny amplitudes).  Bounds
+per precision mode: FP32 and TF32x3 <= 1e-5; BF16x3 <= 2e-5; TF32 <= 5e-3
+(the paper's A100 TF32 result differs from FP32 by 9e-4 relative, Table 2).
+"""
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from oracle import tn as otn
+from workloads import (bell_circuit, ghz_circuit, grid_circuit, inverse_circuit, random_bitstrings)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 2e-5, "tf32": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2104_10523_gb300 import build, tnq
+    build.build()
+    tnq.load()
+    return tnq
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def run(T, circ, bits, precision="fp32", **opts):
+    ctx = T.Context(0, precision)
+    plan = T.Plan(T.Circuit(circ), **opts)
+    ctx.bind(plan)
+    return ctx.amplitudes(plan, bits), plan
+
+
+CONFIG_SMALL_BITS = random_bitstrings(12, 64, 99)
+
+
+@pytest.fixture(scope="module")
+def small_ref():
+    c = grid_circuit(3, 4, 8, 1234)
+    return c, sv.amplitudes(c, CONFIG_SMALL_BITS)
+
+
+@pytest.mark.parametrize("w", [0, 3, 6])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_config_small_fp32(T, small_ref, w, mode):
+    c, ref = small_ref
+    amp, plan = run(T, c, CONFIG_SMALL_BITS, "fp32", batch_log2=w, path_mode=mode, n_candidates=4, seed=1)
+    assert rel_l2(amp, ref) <= TOL["fp32"]
+
+
+def test_config_small_matches_tn_oracle(T, small_ref):
+    c, _ = small_ref
+    ref2 = otn.amplitudes(c, CONFIG_SMALL_BITS[:16])
+    amp, _ = run(T, c, CONFIG_SMALL_BITS[:16], "fp32", batch_log2=4)
+    assert rel_l2(amp, ref2) <= TOL["fp32"]
+
+
+@pytest.mark.parametrize("cap", [6, 9])
+def test_sliced_plans(T, small_ref, cap):
+    c, ref = small_ref
+    amp, plan = run(T, c, CONFIG_SMALL_BITS, "fp32", batch_log2=2, max_intermediate_log2=cap,
+                    path_mode=0)
+    assert plan.info["n_sliced"] >= 1
+    assert plan.info["max_log2"] <= cap
+    assert rel_l2(amp, ref) <= TOL["fp32"]
+
+
+def test_ragged_batch_and_device_buffers(T, small_ref):
+    import torch
+    c, ref = small_ref
+    ctx = T.Context(0, "fp32")
+    plan = T.Plan(T.Circuit(c), batch_log2=4)
+    ctx.bind(plan)
+    bits = torch.from_numpy(CONFIG_SMALL_BITS[:37].copy()).cuda()
+    out = ctx.amplitudes(plan, bits).cpu().numpy()
+    amp = out[:, 0] + 1j * out[:, 1]
+    assert rel_l2(amp, ref[:37]) <= TOL["fp32"]
+    # empty request is a no-op
+    assert ctx.amplitudes(plan, CONFIG_SMALL_BITS[:0]).shape == (0,)
+
+
+def test_bad_bits_rejected(T, small_ref):
+    c, _ = small_ref
+    ctx = T.Context(0, "fp32")
+    plan = T.Plan(T.Circuit(c), batch_log2=2)
+    ctx.bind(plan)
+    bad = CONFIG_SMALL_BITS[:4].copy()
+    bad[1, 3] = 2
+    with pytest.raises(T.TnqError) as e:
+        ctx.amplitudes(plan, bad)
+    assert e.value.status == T.TNQ_ERR_INVALID_ARG
+
+
+def test_unbound_plan_rejected(T, small_ref):
+    c, _ = small_ref
+    ctx = T.Context(0, "fp32")
+    plan = T.Plan(T.Circuit(c))
+    out = np.zeros((1, 2))
+    with pytest.raises(T.TnqError) as e:
+        T.tnq_amplitudes(ctx.h, plan.h, CONFIG_SMALL_BITS[:1], out)
+    assert e.value.status == T.TNQ_ERR_WORKSPACE
+
+
+def test_bell(T):
+    bits = np.array([[0, 0], [1, 1], [0, 1], [1, 0]], dtype=np.int8)
+    amp, _ = run(T, bell_circuit(), bits, "fp32", batch_log2=2)
+    s = 1 / np.sqrt(2)
+    assert np.allclose(amp, [s, s, 0, 0], atol=1e-7)
+
+
+@pytest.mark.parametrize("n", [36, 60])
+def test_ghz_large(T, n):
+    rng = np.random.default_rng(n)
+    bits = rng.integers(0, 2, size=(8, n)).astype(np.int8)
+    bits[0] = 0
+    bits[1] = 1
+    amp, _ = run(T, ghz_circuit(n), bits, "fp32", batch_log2=3)
+    want = np.zeros(8, complex)
+    want[0] = want[1] = 1 / np.sqrt(2)
+    assert np.allclose(amp, want, atol=1e-7)
+
+
+def test_identity_circuit(T):
+    c = inverse_circuit(grid_circuit(3, 4, 6, 77))
+    bits = random_bitstrings(12, 8, 4)
+    bits[0] = 0
+    amp, _ = run(T, c, bits, "fp32", batch_log2=3)
+    want = np.array([1.0 if not b.any() else 0.0 for b in bits])
+    assert np.allclose(amp, want, atol=2e-6)
+
+
+def test_grid_4x5_against_statevector(T):
+    c = grid_circuit(4, 5, 10, 2021)
+    bits = random_bitstrings(20, 256, 77)
+    ref = sv.amplitudes(c, bits)
+    amp, _ = run(T, c, bits, "fp32", batch_log2=8, path_mode=2, n_candidates=8)
+    assert rel_l2(amp, ref) <= TOL["fp32"]
