@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Benchmark: bitstring amplitudes by full tensor-network contraction on GB300.
+
+Workload (default): 6x6 grid random circuit, 14 cycles (sqrt-X/Y/W layers and
+fSim(pi/2, pi/6) on the ABCDCDAB edge patterns), seed 2104; 1024 uniformly
+random bitstrings (seed 10523); contraction path sliced so that no
+intermediate exceeds 2^28 complex64 elements.  One step = one batch of
+2^batch_log2 bitstrings through every slice of the plan (all pairwise
+contractions, the FP64 cross-slice sum, the mapping to bitstring order).
+
+Prints one JSON line (rank 0).  Under torchrun every rank contracts its own
+bitstrings (weak scaling, no collective on the data path); the elapsed time is
+the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+T_START = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - T_START:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
+METRIC = "amplitudes/s and contraction TFLOP/s, mixed vs plain FP32 at ≤1e-5 rel err"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3"])
+    ap.add_argument("--batch-log2", type=int, default=2)
+    ap.add_argument("--candidates", type=int, default=512)
+    ap.add_argument("--cap", type=int, default=28)
+    ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+WORKLOAD = dict(rows=6, cols=6, cycles=14, seed=2104, n_bitstrings=1024, bits_seed=10523)
+
+
+def workload_desc(a):
+    return (f"{WORKLOAD['rows']}x{WORKLOAD['cols']} grid random circuit, {WORKLOAD['cycles']} cycles, "
+            f"{WORKLOAD['n_bitstrings']} random bitstrings, max intermediate 2^{a.cap} complex64")
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def oracle_sample(plan_steps, flops_per_amp, seconds):
+    """Time the oracle's FP64 pairwise contraction (oracle.tn.contract_pair) on
+    random tensors with the plan's step shapes (operands <= 2^22 elements),
+    for about `seconds`; return (amplitudes/s, cores, description)."""
+    import numpy as np
+    from oracle import tn as otn
+    rng = np.random.default_rng(0)
+    shapes = [r for r in plan_steps if max(r[0], r[1]) <= 22]
+    shapes.sort(key=lambda r: -(r[3] + r[4] + r[5] + r[6]))
+    done_flops, t0, n = 0.0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds and shapes:
+        r = shapes[n % len(shapes)]
+        nh, nm, nn, nk = int(r[3]), int(r[4]), int(r[5]), int(r[6])
+        lab_k = list(range(nk))
+        lab_m = list(range(100, 100 + nm))
+        lab_n = list(range(200, 200 + nn))
+        a_lab = lab_k + lab_m
+        b_lab = lab_k + lab_n
+        for h in range(2 ** nh):  # batch labels: one contraction per batch entry
+            A = rng.standard_normal((2,) * len(a_lab)) + 1j * rng.standard_normal((2,) * len(a_lab))
+            B = rng.standard_normal((2,) * len(b_lab)) + 1j * rng.standard_normal((2,) * len(b_lab))
+            otn.contract_pair((A, a_lab), (B, b_lab))
+            done_flops += 8.0 * 2.0 ** (nm + nn + nk)
+            if time.perf_counter() - t0 > seconds:
+                break
+        n += 1
+    dt = time.perf_counter() - t0
+    rate = done_flops / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"oracle FP64 pairwise contraction (np.tensordot) on {n} of the plan's step shapes with operands "
+            f"<= 2^22 elements for {dt:.1f} s: {rate / 1e9:.2f} GFLOP/s, scaled by the plan's "
+            f"{flops_per_amp:.3e} flops per amplitude")
+    return rate / flops_per_amp, cores, desc
+
+
+# ---------------------------------------------------------------- main
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if a.impl == "reference":
+        return run_reference(a, world, rank)
+
+    import numpy as np
+    import torch
+    from paper_2104_10523_gb300 import build, tnq
+    from workloads import grid_circuit, random_bitstrings
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    tnq.load()
+    circ = grid_circuit(WORKLOAD["rows"], WORKLOAD["cols"], WORKLOAD["cycles"], WORKLOAD["seed"])
+    bits_all = random_bitstrings(circ.n, WORKLOAD["n_bitstrings"], WORKLOAD["bits_seed"])
+    B = 2 ** a.batch_log2
+    t_plan = time.perf_counter()
+    plan = tnq.Plan(tnq.Circuit(circ), max_intermediate_log2=a.cap, batch_log2=a.batch_log2,
+                    path_mode=tnq.TNQ_PATH_BEST, n_candidates=a.candidates, seed=7)
+    t_plan = time.perf_counter() - t_plan
+    log(f"plan: {plan.info['n_steps']} steps, 2^{plan.info['n_sliced']} slices, "
+        f"{plan.info['flops_per_batch']:.3e} flops/step, search {t_plan:.1f} s")
+    ctx = tnq.Context(local, a.precision)
+    ctx.bind(plan)
+    info = plan.info
+    stream = ctx.stream
+
+    def batch(i):
+        start = ((rank * (a.steps + a.warmup) + i) * B) % WORKLOAD["n_bitstrings"]
+        idx = [(start + j) % WORKLOAD["n_bitstrings"] for j in range(B)]
+        return bits_all[idx]
+
+    dev_bits = [torch.from_numpy(batch(i)).to(f"cuda:{local}") for i in range(a.warmup + a.steps)]
+    out = torch.empty((B, 2), dtype=torch.float64, device=f"cuda:{local}")
+
+    def step(i):
+        tnq.tnq_amplitudes(ctx.h, plan.h, dev_bits[i], out)
+
+    for i in range(a.warmup):
+        step(i)
+        log(f"warmup step {i} done")
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    n0 = tnq.tnq_ctx_launch_count(ctx.h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(a.warmup, a.warmup + a.steps):
+        step(i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = tnq.tnq_ctx_launch_count(ctx.h) - n0
+    clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+        torch.distributed.barrier()
+    amps = a.steps * B * world
+    value = amps / elapsed
+    flops_step = info["flops_per_batch"]
+    tflops = flops_step * a.steps * world / elapsed / 1e12
+    mixed_amp = out.cpu().numpy()
+
+    log(f"timed steps: {elapsed:.3f} s")
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    host_bits = [torch.from_numpy(batch(i)).pin_memory() for i in range(a.warmup, a.warmup + a.steps)]
+    host_out = torch.empty((B, 2), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for hb in host_bits:
+        tnq.tnq_amplitudes(ctx.h, plan.h, hb, host_out)
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": a.steps * B * world / e2e_t if world == 1 else None, "unit": "amplitudes/s",
+           "h2d_bytes_per_step": int(B * circ.n), "d2h_bytes_per_step": int(B * 16)}
+    if world > 1:
+        t = torch.tensor([e2e_t], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e["value"] = a.steps * B * world / float(t.item())
+
+    log(f"e2e: {e2e_t:.3f} s")
+    # ---- roofline of the dominant kernel: per-launch CUDA events over one more step
+    tnq.tnq_ctx_set_timing(ctx.h, True)
+    step(a.warmup + a.steps - 1)
+    torch.cuda.synchronize()
+    rec = tnq.tnq_ctx_get_timings(ctx.h)
+    tnq.tnq_ctx_set_timing(ctx.h, False)
+    roofline, kernel_share = roofline_of(rec, a.precision)
+
+    log("roofline pass done")
+    # ---- plain FP32 arm on the same plan and the same batch
+    compare = None
+    if not a.skip_fp32:
+        ctx32 = tnq.Context(local, "fp32")
+        ctx32.bind(plan)
+        last = a.warmup + a.steps - 1
+        tnq.tnq_amplitudes(ctx32.h, plan.h, dev_bits[last], out)  # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tnq.tnq_amplitudes(ctx32.h, plan.h, dev_bits[last], out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1) / 1e3
+        fp32_amp = out.cpu().numpy()
+        diff = np.linalg.norm(mixed_amp - fp32_amp) / np.linalg.norm(fp32_amp)
+        compare = {"fp32_value": B / t32, "fp32_tflops": flops_step / t32 / 1e12,
+                   "speedup_vs_fp32": value / world / (B / t32), "rel_l2_vs_fp32": float(diff)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
+        "config": {"workload": workload_desc(a), "bitstrings_per_step": B, "slices": 2 ** info["n_sliced"],
+                   "max_intermediate_log2": info["max_log2"], "flops_per_step": flops_step,
+                   "path_search_s": round(t_plan, 2), "l2": "working set larger than L2 (intermediates up to "
+                   f"2^{info['max_log2']} x 8 B)", "parallelism": f"dp{world} (independent bitstrings)"},
+        "contraction_tflops": tflops,
+        "roofline": roofline,
+        "kernel_share": kernel_share,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+        "compare": compare,
+    }
+    log("fp32 arm done")
+    if rank == 0:
+        rate, cores, desc = oracle_sample(plan.steps().tolist(), flops_step / B, a.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline_of(rec, precision):
+    """Dominant kernel by total time; its achieved rate against the measured peak."""
+    import numpy as np
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        src = "measured"
+    except OSError:
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+        src = "fallback"
+    if len(rec) == 0:
+        return None, None
+    kinds = {0: "permute", 1: "cgemm_simt", 2: "cgemm_tc", 3: "other", 4: "cgemm_skinny"}
+    tot = {}
+    for r in rec:
+        k = int(r[0])
+        t = tot.setdefault(k, [0.0, 0.0, 0.0, 0])
+        t[0] += r[8]
+        t[1] += r[6]
+        t[2] += r[7]
+        t[3] += 1
+    all_ms = sum(v[0] for v in tot.values())
+    share = {kinds[k]: round(v[0] / all_ms, 4) for k, v in tot.items()}
+    k = max(tot, key=lambda x: tot[x][0])
+    ms, flops, nbytes, n = tot[k]
+    bf16_sus = float(peaks.get("bf16_tflops_sustained", 1720.9))
+    traffic = load_traffic(kinds[k])
+    if k == 2:
+        # tensor-pipe peak of the mode: TF32 runs at half the BF16 rate (nominal 1.1 vs 2.25 PF/s);
+        # the split modes issue three products per useful product.
+        per_mode = {"tf32": bf16_sus * 1.1 / 2.25, "tf32x3": bf16_sus * 1.1 / 2.25 / 3,
+                    "bf16x3": bf16_sus / 3}
+        peak = per_mode.get(precision, bf16_sus)
+        ach = flops / (ms / 1e3) / 1e12
+        return ({"kernel": "cgemm_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                 "frac": ach / peak, "traffic": traffic, "launches": n, "avg_launch_ms": ms / n,
+                 "peak_source": f"{src} bf16 sustained, mode-adjusted"}, share)
+    if k == 1:
+        # FP32 FFMA roof: 152 SMs x 128 lanes x 2 flops x max SM clock
+        peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        ach = flops / (ms / 1e3) / 1e12
+        return ({"kernel": "cgemm_simt", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                 "frac": ach / peak, "traffic": traffic, "launches": n, "avg_launch_ms": ms / n,
+                 "peak_source": "FFMA lanes x max clock"}, share)
+    ach = nbytes / (ms / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    return ({"kernel": kinds[k], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+             "traffic": traffic, "launches": n, "avg_launch_ms": ms / n, "peak_source": f"{src} copy"}, share)
+
+
+def load_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2104_10523_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+def run_reference(a, world, rank):
+    """The oracle on the host cores, same workload, metric and unit; bounded sample per step."""
+    if rank != 0:
+        return
+    from paper_2104_10523_gb300 import build, tnq
+    from workloads import grid_circuit
+    build.build()
+    tnq.load()
+    circ = grid_circuit(WORKLOAD["rows"], WORKLOAD["cols"], WORKLOAD["cycles"], WORKLOAD["seed"])
+    B = 2 ** a.batch_log2
+    plan = tnq.Plan(tnq.Circuit(circ), max_intermediate_log2=a.cap, batch_log2=a.batch_log2,
+                    path_mode=tnq.TNQ_PATH_BEST, n_candidates=a.candidates, seed=7)
+    steps = plan.steps().tolist()
+    per_amp = plan.info["flops_per_batch"] / B
+    per_step = max(2.0, min(a.cpu_seconds, 120.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        oracle_sample(steps, per_amp, per_step / 4)
+    rates = []
+    desc, cores = "", 1
+    for _ in range(a.steps):
+        r, cores, desc = oracle_sample(steps, per_amp, per_step)
+        rates.append(r)
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": B / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(a), "bitstrings_per_step": B},
+            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

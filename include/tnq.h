@@ -186,6 +186,21 @@ tnq_status tnq_contract_pair(tnq_ctx* ctx, const void* A, int ra, const int* a_l
                              const void* B, int rb, const int* b_labels, void* C, int rc,
                              const int* c_labels, void* workspace, size_t workspace_bytes);
 
+/* ---- measurement ---------------------------------------------------------- */
+/* Number of kernels this context has launched so far (cumulative). */
+tnq_status tnq_ctx_launch_count(const tnq_ctx* ctx, uint64_t* count);
+/* Enable (1) or disable (0) per-kernel timing: every kernel the context
+ * launches is bracketed by CUDA events on its stream, and one record per
+ * launch is kept (enabling clears earlier records).  These per-step timings
+ * (shape, algorithmic flops and bytes, duration) are also the training data
+ * of the learned path cost model. */
+tnq_status tnq_ctx_set_timing(tnq_ctx* ctx, int enable);
+/* Copy up to max_records records, 10 doubles each:
+ * {kind (0 permute, 1 CUDA-core GEMM, 2 tensor-core GEMM, 3 other), plan step,
+ *  log2 H, log2 M, log2 N, log2 K, algorithmic flops, algorithmic bytes,
+ *  milliseconds, 0}.  *n_out receives the number available. */
+tnq_status tnq_ctx_get_timings(const tnq_ctx* ctx, double* rec, int max_records, int* n_out);
+
 #ifdef __cplusplus
 }
 #endif

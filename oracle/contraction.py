@@ -22,16 +22,14 @@ def _as_axes(flat: np.ndarray, labels):
 
 
 def contract_labeled(A: np.ndarray, a_labels, B: np.ndarray, b_labels, out_labels) -> np.ndarray:
-    """sum over shared labels of A * B, as a flat complex128 array with
-    out_labels[p] on bit p.  Every label must appear in A or B; shared labels
-    absent from out_labels are summed."""
+    """C[out] = sum over every label not in out_labels of A * B, as a flat
+    complex128 array with out_labels[p] on bit p.  A label held by A, B and
+    the output is a batch index (not summed)."""
     At, ax_a = _as_axes(np.asarray(A, np.complex128), a_labels)
     Bt, ax_b = _as_axes(np.asarray(B, np.complex128), b_labels)
-    shared = [l for l in ax_a if l in ax_b and l not in out_labels]
-    C = np.tensordot(At, Bt, axes=([ax_a.index(l) for l in shared], [ax_b.index(l) for l in shared]))
-    have = [l for l in ax_a if l not in shared] + [l for l in ax_b if l not in shared]
+    ids = {l: i for i, l in enumerate(sorted(set(ax_a) | set(ax_b)))}
     want = list(reversed(out_labels))
-    C = np.transpose(C, [have.index(l) for l in want]) if want else C
+    C = np.einsum(At, [ids[l] for l in ax_a], Bt, [ids[l] for l in ax_b], [ids[l] for l in want])
     return np.ascontiguousarray(C).reshape(-1)
 
 

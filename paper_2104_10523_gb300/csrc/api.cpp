@@ -213,7 +213,11 @@ tnq_status tnq_ctx_create(const tnq_options* o, tnq_ctx** out) {
   return TNQ_OK;
 }
 
-void tnq_ctx_destroy(tnq_ctx* c) { delete c; }
+void tnq_ctx_destroy(tnq_ctx* c) {
+  if (!c) return;
+  for (auto e : c->c.ev_pool) cudaEventDestroy(e);
+  delete c;
+}
 
 tnq_status tnq_ctx_set_precision(tnq_ctx* c, int precision) {
   if (!c) return fail(TNQ_ERR_INVALID_ARG, "NULL context");
@@ -248,6 +252,42 @@ tnq_status tnq_contract_pair(tnq_ctx* c, const void* A, int ra, const int* al, c
   if (!c || !A || !B || !C) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
   if ((ra && !al) || (rb && !bl) || (rc && !cl)) return fail(TNQ_ERR_INVALID_ARG, "NULL label array");
   return exec_contract_pair(&c->c, A, ra, al, B, rb, bl, C, rc, cl, ws, ws_bytes);
+}
+
+tnq_status tnq_ctx_launch_count(const tnq_ctx* c, uint64_t* count) {
+  if (!c || !count) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  *count = c->c.launches;
+  return TNQ_OK;
+}
+
+tnq_status tnq_ctx_set_timing(tnq_ctx* c, int enable) {
+  if (!c) return fail(TNQ_ERR_INVALID_ARG, "NULL context");
+  c->c.timing = enable != 0;
+  if (enable) {
+    c->c.records.clear();
+    c->c.pending.clear();
+  }
+  return TNQ_OK;
+}
+
+tnq_status tnq_ctx_get_timings(const tnq_ctx* c, double* rec, int max_records, int* n_out) {
+  if (!c || !n_out || (max_records > 0 && !rec)) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  const auto& R = c->c.records;
+  *n_out = (int)R.size();
+  for (int i = 0; i < max_records && i < (int)R.size(); ++i) {
+    double* r = rec + 10 * size_t(i);
+    r[0] = R[i].kind;
+    r[1] = R[i].step;
+    r[2] = R[i].nH;
+    r[3] = R[i].nM;
+    r[4] = R[i].nN;
+    r[5] = R[i].nK;
+    r[6] = R[i].flops;
+    r[7] = R[i].bytes;
+    r[8] = R[i].ms;
+    r[9] = 0;
+  }
+  return TNQ_OK;
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 // the batch accumulator (the cross-slice sum, fixed ascending slice order).
 // The accumulator is finally mapped to bitstring order.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -15,6 +16,7 @@
 #include "kernels.cuh"
 #include "gemm_tc.cuh"
 #include "traj.cuh"
+#include "splitk.h"
 
 namespace tnq {
 
@@ -27,6 +29,38 @@ tnq_status cuda_fail(cudaError_t e, const char* what) {
     cudaError_t _e = (call);                            \
     if (_e != cudaSuccess) return cuda_fail(_e, #call); \
   } while (0)
+
+int timing_begin(Ctx* ctx) {
+  if (!ctx->timing) return -1;
+  size_t need = ctx->pending.size() * 2 + 2;
+  while (ctx->ev_pool.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    ctx->ev_pool.push_back(e);
+  }
+  int slot = (int)ctx->pending.size() * 2;
+  cudaEventRecord(ctx->ev_pool[slot], ctx->stream);
+  return slot;
+}
+
+void timing_end(Ctx* ctx, int slot, const KernelRecord& r) {
+  if (slot < 0) return;
+  cudaEventRecord(ctx->ev_pool[slot + 1], ctx->stream);
+  ctx->pending.push_back({slot, r});
+}
+
+tnq_status timing_collect(Ctx* ctx) {
+  for (auto& pr : ctx->pending) {
+    float ms = 0;
+    cudaError_t e = cudaEventElapsedTime(&ms, ctx->ev_pool[pr.first], ctx->ev_pool[pr.first + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    KernelRecord r = pr.second;
+    r.ms = ms;
+    ctx->records.push_back(r);
+  }
+  ctx->pending.clear();
+  return TNQ_OK;
+}
 
 namespace {
 
@@ -67,21 +101,77 @@ struct StepOperands {
   const void* b1 = nullptr;
 };
 
+cudaError_t perm(Ctx* ctx, const PermDesc& d, const void* src, void* dst0, void* dst1, int slice_id,
+               double bytes) {
+  KernelRecord r{0, ctx->cur_step, 0, 0, 0, 0, 0.0, bytes, 0.f};
+  int slot = timing_begin(ctx);
+  cudaError_t e = launch_permute(d, src, dst0, dst1, slice_id, ctx->sm_count, ctx->stream);
+  timing_end(ctx, slot, r);
+  ctx->launches++;
+  return e;
+}
+
 // Prepare operands (permute / convert) and run one batched complex GEMM.
 tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_labels, bool perm_a,
                          const void* b_src, const std::vector<int>& b_labels, bool perm_b,
                          const std::vector<int>& a_req, const std::vector<int>& b_req,
                          const std::vector<int>& slice_labels, int slice_id, int nH, int nM, int nN, int nK,
-                         char* scratch_a, char* scratch_b, void* C, void* acc) {
-  const int prec = ctx->precision;
+                         char* scratch_a, char* scratch_b, void* C, void* acc, int* err, void* part) {
+  // Small, skinny or K-degenerate steps run on the CUDA cores in FP32 whatever
+  // the mode: they are launch- or bandwidth-bound and a tensor-core tile would idle.
+  const double work = std::ldexp(1.0, nH + nM + nN + nK);
+  const bool use_tc = ctx->precision != TNQ_PREC_FP32 && !skinny(nM, nN) &&
+                      tc_gemm_supported(1 << nM, 1 << nN, 1 << nK, ctx->precision) && work >= ctx->tc_min_work;
+  const size_t out_elems = size_t(1) << (nH + nM + nN);
+  const int prec = use_tc ? ctx->precision : TNQ_PREC_FP32;
   StepOperands op;
   PermDesc d;
   const int ns = (int)slice_labels.size();
+  if (!use_tc && (skinny(nM, nN) || use_dot(nM, nN, nK)) && part) {
+    // bandwidth-bound skinny step: complex64 operands in [h][m|n][k] order
+    if (perm_a) {
+      build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(),
+                      ns, PM_C64, nK, &d);
+      TNQ_CUDA(perm(ctx, d, a_src, scratch_a, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)a_req.size())));
+    }
+    if (perm_b) {
+      build_perm_desc(b_labels.data(), (int)b_labels.size(), b_req.data(), (int)b_req.size(), slice_labels.data(),
+                      ns, PM_C64, nK, &d);
+      TNQ_CUDA(perm(ctx, d, b_src, scratch_b, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)b_req.size())));
+    }
+    const void* A = perm_a ? (const void*)scratch_a : a_src;
+    const void* B = perm_b ? (const void*)scratch_b : b_src;
+    const int M = 1 << nM, N = 1 << nN, K = 1 << nK, H = 1 << nH;
+    KernelRecord r{4, ctx->cur_step, nH, nM, nN, nK, 8.0 * work,
+                   8.0 * (std::ldexp(1.0, nH + nM + nK) + std::ldexp(1.0, nH + nN + nK) +
+                          (acc ? 2.0 : 1.0) * std::ldexp(1.0, nH + nM + nN)),
+                   0.f};
+    int slot = timing_begin(ctx);
+    cudaError_t e;
+    int splits;
+    if (use_dot(nM, nN, nK)) {
+      splits = dot_splits(nH, nM, nN, nK);
+      e = launch_cdot(A, B, part, splits, M, N, K, H, ctx->stream);
+      if (e == cudaSuccess) e = launch_reduce_splits(part, splits, out_elems, C, acc, ctx->sm_count, ctx->stream);
+    } else {
+      splits = rows_splits(nH, nM, nN, nK);
+      if (nM <= nN)
+        e = launch_cgemm_rows(A, B, C, acc, part, splits, M, N, K, H, N, 1, ctx->stream);
+      else
+        e = launch_cgemm_rows(B, A, C, acc, part, splits, N, M, K, H, 1, N, ctx->stream);
+      if (e == cudaSuccess && splits > 1)
+        e = launch_reduce_splits(part, splits, out_elems, C, acc, ctx->sm_count, ctx->stream);
+    }
+    timing_end(ctx, slot, r);
+    TNQ_CUDA(e);
+    ctx->launches += (use_dot(nM, nN, nK) || splits > 1) ? 2 : 1;
+    return TNQ_OK;
+  }
   if (prec == TNQ_PREC_FP32) {
     if (perm_a) {
       build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(),
                       ns, PM_C64, nK, &d);
-      TNQ_CUDA(launch_permute(d, a_src, scratch_a, nullptr, slice_id, ctx->sm_count, ctx->stream));
+      TNQ_CUDA(perm(ctx, d, a_src, scratch_a, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)a_req.size())));
       op.a0 = scratch_a;
     } else {
       op.a0 = a_src;
@@ -89,12 +179,24 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
     if (perm_b) {
       build_perm_desc(b_labels.data(), (int)b_labels.size(), b_req.data(), (int)b_req.size(), slice_labels.data(),
                       ns, PM_C64, nK, &d);
-      TNQ_CUDA(launch_permute(d, b_src, scratch_b, nullptr, slice_id, ctx->sm_count, ctx->stream));
+      TNQ_CUDA(perm(ctx, d, b_src, scratch_b, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)b_req.size())));
       op.b0 = scratch_b;
     } else {
       op.b0 = b_src;
     }
-    TNQ_CUDA(launch_cgemm_simt(op.a0, op.b0, C, acc, 1 << nM, 1 << nN, 1 << nK, 1 << nH, ctx->stream));
+    KernelRecord r{1, ctx->cur_step, nH, nM, nN, nK, 8.0 * work,
+                   8.0 * (std::ldexp(1.0, nH + nM + nK) + std::ldexp(1.0, nH + nN + nK) +
+                          (acc ? 2.0 : 1.0) * std::ldexp(1.0, nH + nM + nN)),
+                   0.f};
+    const int splits = part ? simt_splits(nH, nM, nN, nK) : 1;
+    int slot = timing_begin(ctx);
+    TNQ_CUDA(launch_cgemm_simt(op.a0, op.b0, C, acc, part, splits, 1 << nM, 1 << nN, 1 << nK, 1 << nH, ctx->stream));
+    if (splits > 1) {
+      TNQ_CUDA(launch_reduce_splits(part, splits, out_elems, C, acc, ctx->sm_count, ctx->stream));
+      ctx->launches++;
+    }
+    timing_end(ctx, slot, r);
+    ctx->launches++;
     return TNQ_OK;
   }
   // tensor-core modes: A is always expanded (and split), B split unless plain TF32 in place
@@ -102,7 +204,7 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
   build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(), ns,
                   tc_mode_a(prec), nK, &d);
   char* a1 = scratch_a + ((a_half_bytes(prec, na) + 1023) & ~size_t(1023));
-  TNQ_CUDA(launch_permute(d, a_src, scratch_a, a1, slice_id, ctx->sm_count, ctx->stream));
+  TNQ_CUDA(perm(ctx, d, a_src, scratch_a, a1, slice_id, 8.0 * na + a_half_bytes(prec, na) * (prec == TNQ_PREC_TF32 ? 1 : 2)));
   op.a0 = scratch_a;
   op.a1 = prec == TNQ_PREC_TF32 ? nullptr : a1;
   if (prec == TNQ_PREC_TF32 && !perm_b) {
@@ -111,7 +213,7 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
     build_perm_desc(b_labels.data(), (int)b_labels.size(), b_req.data(), (int)b_req.size(), slice_labels.data(),
                     ns, tc_mode_b(prec), nK, &d);
     char* b1 = scratch_b + ((b_half_bytes(prec, nb) + 1023) & ~size_t(1023));
-    TNQ_CUDA(launch_permute(d, b_src, scratch_b, b1, slice_id, ctx->sm_count, ctx->stream));
+    TNQ_CUDA(perm(ctx, d, b_src, scratch_b, b1, slice_id, 8.0 * nb + b_half_bytes(prec, nb) * (prec == TNQ_PREC_TF32 ? 1 : 2)));
     op.b0 = scratch_b;
     op.b1 = prec == TNQ_PREC_TF32 ? nullptr : b1;
   }
@@ -127,15 +229,35 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
   g.K = 1 << nK;
   g.batch = 1 << nH;
   g.precision = prec;
+  g.err = err;
+  int used = 1;
+  g.splits = part ? tc_splits(nH, nM, nN, nK, prec == TNQ_PREC_BF16X3) : 1;
+  g.part = part;
+  g.splits_used = &used;
+  const double op_bytes = prec == TNQ_PREC_BF16X3 ? 2.0 : 4.0;
+  const double npass = prec == TNQ_PREC_TF32 ? 1.0 : 2.0;
+  KernelRecord r{2, ctx->cur_step, nH, nM, nN, nK, 8.0 * work,
+                 npass * op_bytes * (4.0 * std::ldexp(1.0, nH + nM + nK) + 2.0 * std::ldexp(1.0, nH + nN + nK)) +
+                     (acc ? 16.0 : 8.0) * std::ldexp(1.0, nH + nM + nN),
+                 0.f};
+  int slot = timing_begin(ctx);
   cudaError_t e = launch_cgemm_tc(g, ctx->sm_count, ctx->stream);
+  if (e == cudaSuccess && used > 1) {
+    e = launch_reduce_splits(part, used, out_elems, C, acc, ctx->sm_count, ctx->stream);
+    ctx->launches++;
+  }
+  timing_end(ctx, slot, r);
   if (e == cudaErrorNotSupported)
     return fail(TNQ_ERR_NOT_SUPPORTED, "tensor-core GEMM unavailable for this shape/precision");
   TNQ_CUDA(e);
+  ctx->launches++;
   return TNQ_OK;
 }
 
 tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws) {
-  for (auto& s : p->steps) {
+  for (size_t si = 0; si < p->steps.size(); ++si) {
+    auto& s = p->steps[si];
+    ctx->cur_step = (int)si;
     auto& ta = p->tensors[s.a];
     auto& tb = p->tensors[s.b];
     void* acc = s.out == p->root ? (void*)(ws + p->ws_acc) : nullptr;
@@ -143,9 +265,11 @@ tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws) {
     tnq_status st = run_gemm_step(ctx, ws + ta.offset, ta.labels, s.perm_a,
                                   ws + tb.offset, tb.labels, s.perm_b,
                                   s.a_req, s.b_req, p->slice_labels, slice_id, s.nH, s.nM, s.nN, s.nK,
-                                  ws + p->ws_scratch_a, ws + p->ws_scratch_b, C, acc);
+                                  ws + p->ws_scratch_a, ws + p->ws_scratch_b, C, acc,
+                                  reinterpret_cast<int*>(ws + p->ws_misc + 4), ws + p->ws_partial);
     if (st != TNQ_OK) return st;
   }
+  ctx->cur_step = -1;
   return TNQ_OK;
 }
 
@@ -204,7 +328,7 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
   const auto& rl = p->tensors[p->root].labels;
   for (int j = 0; j < w; ++j)
     pos[j] = int(std::find(rl.begin(), rl.end(), p->net.batch_labels[j]) - rl.begin());
-  TNQ_CUDA(cudaMemsetAsync(err_flag, 0, sizeof(int), ctx->stream));
+  TNQ_CUDA(cudaMemsetAsync(err_flag, 0, 2 * sizeof(int), ctx->stream));
   const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
   const int n_slices = 1 << p->slice_labels.size();
   for (int64_t base = 0; base < n_bs; base += per) {
@@ -217,6 +341,7 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
       bsrc = bits_stage;
     }
     TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w, bsrc, nv, err_flag, ctx->stream));
+    ctx->launches++;
     TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
     for (int s = 0; s < n_slices; ++s) {
       tnq_status st = run_pass(ctx, p, s, ws);
@@ -224,13 +349,19 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
     }
     double* dst = out_dev ? out + 2 * base : out_stage;
     TNQ_CUDA(launch_finalize(ws + p->ws_acc, dst, nv, pos.data(), w, ctx->stream));
+    ctx->launches++;
     if (!out_dev)
       TNQ_CUDA(cudaMemcpyAsync(out + 2 * base, out_stage, size_t(nv) * 16, cudaMemcpyDeviceToHost, ctx->stream));
   }
-  int herr = 0;
-  TNQ_CUDA(cudaMemcpyAsync(&herr, err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int herr[2] = {0, 0};
+  TNQ_CUDA(cudaMemcpyAsync(herr, err_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
-  if (herr) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  if (ctx->timing) {
+    tnq_status ts = timing_collect(ctx);
+    if (ts != TNQ_OK) return ts;
+  }
+  if (herr[1]) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired; results are invalid");
+  if (herr[0]) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
   return TNQ_OK;
 }
 
@@ -247,10 +378,16 @@ tnq_status exec_noisy(Ctx* ctx, Plan* p, int64_t n_traj, uint64_t seed, int64_t 
   return fail(TNQ_ERR_NOT_SUPPORTED, "noisy trajectories not built yet");
 }
 
+// Partial-product bytes any split of an output of 2^rc elements can need.
+static size_t partial_bound(int rc) {
+  double e = std::min(kPartialCapElems, std::ldexp(1.0, rc) * 1024.0);
+  return size_t(8 * e);
+}
+
 size_t contract_workspace_bytes(int precision, int ra, int rb, int rc) {
   (void)precision;
   size_t na = size_t(1) << std::max(ra, rb), nb = na;
-  return 32 * na + 16 * nb + 8 * (size_t(1) << rc) + 3 * 4096;
+  return 32 * na + 16 * nb + 8 * (size_t(1) << rc) + partial_bound(rc) + 5 * 4096;
 }
 
 tnq_status exec_contract_pair(Ctx* ctx, const void* A, int ra, const int* al, const void* B, int rb,
@@ -298,18 +435,28 @@ tnq_status exec_contract_pair(Ctx* ctx, const void* A, int ra, const int* al, co
   char* sa = w;
   char* sb = w + ((32 * na + 4095) & ~size_t(4095));
   char* sc = sb + ((16 * na + 4095) & ~size_t(4095));
+  int* err = reinterpret_cast<int*>(sc + ((8 * (size_t(1) << rc) + 4095) & ~size_t(4095)));
+  char* part = reinterpret_cast<char*>(err) + 4096;
+  TNQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
   bool direct = out == lc;
   std::vector<int> none;
   tnq_status st = run_gemm_step(ctx, pa, xa, xa != a_req, pb, xb, xb != b_req, a_req, b_req, none, 0,
                                 (int)Hh.size(), (int)M.size(), (int)N.size(), (int)K.size(), sa, sb,
-                                direct ? C : (void*)sc, nullptr);
+                                direct ? C : (void*)sc, nullptr, err, part);
   if (st != TNQ_OK) return st;
   if (!direct) {
     PermDesc d;
     build_perm_desc(out.data(), (int)out.size(), lc.data(), rc, nullptr, 0, PM_C64, 0, &d);
-    TNQ_CUDA(launch_permute(d, sc, C, nullptr, 0, ctx->sm_count, ctx->stream));
+    TNQ_CUDA(perm(ctx, d, sc, C, nullptr, 0, 16.0 * std::ldexp(1.0, rc)));
   }
+  int herr = 0;
+  TNQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->timing) {
+    tnq_status ts = timing_collect(ctx);
+    if (ts != TNQ_OK) return ts;
+  }
+  if (herr) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired; results are invalid");
   return TNQ_OK;
 }
 

@@ -8,12 +8,34 @@
 
 namespace tnq {
 
+// One kernel launch as seen by the optional timing recorder.
+struct KernelRecord {
+  int kind;        // 0 permute, 1 SIMT GEMM, 2 tensor-core GEMM, 3 other, 4 skinny (rows/dot) GEMM
+  int step;        // plan step index (-1 outside a plan)
+  int nH, nM, nN, nK;
+  double flops;    // algorithmic flops (8 per complex multiply-add)
+  double bytes;    // algorithmic bytes moved
+  float ms;        // CUDA-event duration on the launching stream
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int precision = TNQ_PREC_FP32;
   int sm_count = 0;
+  double tc_min_work = 1 << 18;  // complex MACs below which a step stays on the CUDA cores
+  uint64_t launches = 0;         // kernels launched by this context (cumulative)
+  bool timing = false;           // record CUDA events around every kernel
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, KernelRecord>> pending;  // (event index, record)
+  std::vector<KernelRecord> records;
+  int cur_step = -1;
 };
+
+// Timing helpers: bracket a launch when ctx->timing is set.
+int timing_begin(Ctx* ctx);
+void timing_end(Ctx* ctx, int slot, const KernelRecord& r);
+tnq_status timing_collect(Ctx* ctx);  // after a stream sync
 
 tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes);
 tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, double* out);

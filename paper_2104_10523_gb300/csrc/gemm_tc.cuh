@@ -17,7 +17,14 @@ struct TcGemmArgs {
   void* acc = nullptr;         // complex128 accumulator (added to) when non-null
   int M = 0, N = 0, K = 0, batch = 1;
   int precision = 0;           // tnq_precision
+  int* err = nullptr;          // device flag, set when a bounded wait runs out
+  int splits = 1;              // requested K splits (partials to `part`, reduced by the caller)
+  void* part = nullptr;        // FP32 partials [splits][batch][M][N] complex
+  int* splits_used = nullptr;  // out: splits actually launched
 };
+
+// Whether a GEMM of this shape and precision runs on the tensor cores.
+bool tc_gemm_supported(int M, int N, int K, int precision);
 
 // Returns cudaErrorNotSupported when the shape cannot run on the tensor cores.
 cudaError_t launch_cgemm_tc(const TcGemmArgs& g, int sm_count, cudaStream_t st);

@@ -129,7 +129,7 @@ struct Plan {
   int batch_log2 = 0, traj_log2 = 0;
   int root = -1;
   // workspace layout (bytes)
-  size_t ws_leaves = 0, ws_arena = 0, ws_arena_bytes = 0, ws_scratch_a = 0, ws_scratch_b = 0,
+  size_t ws_leaves = 0, ws_arena = 0, ws_arena_bytes = 0, ws_scratch_a = 0, ws_scratch_b = 0, ws_partial = 0,
          ws_scratch_bytes = 0, ws_acc = 0, ws_misc = 0, ws_total = 0;
   int max_operand_log2 = 0;
   // device binding

@@ -211,8 +211,9 @@ cudaError_t launch_permute(const PermDesc& d, const void* src, void* dst0, void*
 constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16;
 
 __global__ void __launch_bounds__(256) cgemm_simt_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                         float2* __restrict__ C, double2* __restrict__ acc, int M,
-                                                         int N, int K, int batch) {
+                                                         float2* __restrict__ C, double2* __restrict__ acc,
+                                                         float2* __restrict__ part, int M, int N, int K, int batch,
+                                                         int kchunk) {
   __shared__ float2 As[SG_BK][SG_BM + 1];
   __shared__ float2 Bs[SG_BK][SG_BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -226,13 +227,14 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(const float2* __restric
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) cr[i][j] = ci[i][j] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += SG_BK) {
+    const int kbeg = blockIdx.y * kchunk, kend = min(K, kbeg + kchunk);
+    for (int k0 = kbeg; k0 < kend; k0 += SG_BK) {
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         int idx = tid + 256 * l, r = idx >> 4, kk = idx & 15;
         float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
-        if (m0 + r < M && k0 + kk < K) va = Ah[size_t(m0 + r) * K + k0 + kk];
-        if (n0 + r < N && k0 + kk < K) vb = Bh[size_t(n0 + r) * K + k0 + kk];
+        if (m0 + r < M && k0 + kk < kend) va = Ah[size_t(m0 + r) * K + k0 + kk];
+        if (n0 + r < N && k0 + kk < kend) vb = Bh[size_t(n0 + r) * K + k0 + kk];
         As[kk][r] = va;
         Bs[kk][r] = vb;
       }
@@ -263,7 +265,9 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(const float2* __restric
         int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
         if (m < M && n < N) {
           size_t o = size_t(h) * M * N + size_t(m) * N + n;
-          if (acc) {
+          if (part) {
+            part[size_t(blockIdx.y) * batch * M * N + o] = make_float2(cr[i][j], ci[i][j]);
+          } else if (acc) {
             double2 t = acc[o];
             t.x += (double)cr[i][j];
             t.y += (double)ci[i][j];
@@ -276,14 +280,53 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(const float2* __restric
   }
 }
 
-cudaError_t launch_cgemm_simt(const void* A, const void* B, void* C, void* acc, int M, int N, int K,
-                              int batch, cudaStream_t st) {
+cudaError_t launch_cgemm_simt(const void* A, const void* B, void* C, void* acc, void* part, int splits, int M,
+                              int N, int K, int batch, cudaStream_t st) {
   size_t tiles = size_t((N + SG_BN - 1) / SG_BN) * size_t((M + SG_BM - 1) / SG_BM);
-  if (tiles > 0x7fffffffu) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)tiles, 1, std::min(batch, 65535));
+  if (tiles > 0x7fffffffu || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
+  // each split covers a whole number of 16-deep K slices
+  int kchunk = ((K + splits - 1) / splits + SG_BK - 1) / SG_BK * SG_BK;
+  dim3 grid((unsigned)tiles, (unsigned)splits, std::min(batch, 65535));
   cgemm_simt_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(B),
-                                          reinterpret_cast<float2*>(C), reinterpret_cast<double2*>(acc), M, N,
-                                          K, batch);
+                                          reinterpret_cast<float2*>(C), reinterpret_cast<double2*>(acc),
+                                          splits > 1 ? reinterpret_cast<float2*>(part) : nullptr, M, N, K, batch,
+                                          kchunk);
+  return cudaGetLastError();
+}
+
+// out = sum over s of part[s] in ascending s (FP32), or acc += that sum in FP64.
+__global__ void reduce_splits_kernel(const float2* __restrict__ part, int splits, size_t n, float2* __restrict__ C,
+                                     double2* __restrict__ acc) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    if (acc) {
+      double re = 0, im = 0;
+      for (int s = 0; s < splits; ++s) {
+        float2 v = part[size_t(s) * n + i];
+        re += v.x;
+        im += v.y;
+      }
+      double2 t = acc[i];
+      t.x += re;
+      t.y += im;
+      acc[i] = t;
+    } else {
+      float re = 0.f, im = 0.f;
+      for (int s = 0; s < splits; ++s) {
+        float2 v = part[size_t(s) * n + i];
+        re += v.x;
+        im += v.y;
+      }
+      C[i] = make_float2(re, im);
+    }
+  }
+}
+
+cudaError_t launch_reduce_splits(const void* part, int splits, size_t n, void* C, void* acc, int sm_count,
+                                 cudaStream_t st) {
+  size_t blocks = std::min<size_t>((n + 255) / 256, size_t(sm_count) * 8);
+  if (blocks < 1) blocks = 1;
+  reduce_splits_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const float2*>(part), splits, n,
+                                                         reinterpret_cast<float2*>(C), reinterpret_cast<double2*>(acc));
   return cudaGetLastError();
 }
 

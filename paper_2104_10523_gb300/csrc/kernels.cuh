@@ -42,8 +42,21 @@ cudaError_t launch_permute(const PermDesc& d, const void* src, void* dst0, void*
 
 // C[h][m][n] = sum_k A[h][m][k] * B[h][n][k] (complex64, FP32 FFMA); with acc
 // non-null the result is added in FP64 to acc (same layout) instead of stored.
-cudaError_t launch_cgemm_simt(const void* A, const void* B, void* C, void* acc, int M, int N, int K,
-                              int batch, cudaStream_t st);
+// With splits > 1 the K range is cut into `splits` parts whose FP32 partial
+// products go to part[s][h][m][n]; launch_reduce_splits then forms C or acc.
+cudaError_t launch_cgemm_simt(const void* A, const void* B, void* C, void* acc, void* part, int splits, int M,
+                              int N, int K, int batch, cudaStream_t st);
+cudaError_t launch_reduce_splits(const void* part, int splits, size_t n, void* C, void* acc, int sm_count,
+                                 cudaStream_t st);
+
+// Skinny steps (see skinny.cu).  rows: C = S x G^T for a small operand S of
+// ns <= 16 rows; output element (h, s, g) at h*ns*ng + s*s_stride + g*g_stride.
+// dot: M, N <= 4; always writes FP32 partials [splits][batch][M][N].
+cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, void* acc, void* part, int splits,
+                              int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
+                              cudaStream_t st);
+cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, int M, int N, int K, int batch,
+                        cudaStream_t st);
 
 // Projection leaves: P_q[(b << 1) | x] = [bits[(base+b)*n + q] == x] for b < n_valid, else 0.
 cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_qubits, int batch_log2,

@@ -10,12 +10,15 @@
 // Sliced labels are fixed per pass (Sec. 3.1 slicing); only leaves hold them,
 // and a leaf holding one is always gathered through the permute kernel.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <map>
 #include <random>
 
 #include "internal.h"
+#include "splitk.h"
 
 namespace tnq {
 
@@ -155,6 +158,17 @@ void layout_steps(Plan* p) {
   p->ws_scratch_b = off;
   off = align_up(off + 16 * max_b + 4096, 1024);
   p->ws_scratch_bytes = 32 * max_a + 16 * max_b;
+  // FP32 partial products of split-K steps (largest need over steps and kernels)
+  size_t max_part = 0;
+  for (auto& s : p->steps) {
+    int sp = std::max({simt_splits(s.nH, s.nM, s.nN, s.nK), tc_splits(s.nH, s.nM, s.nN, s.nK, true),
+                       tc_splits(s.nH, s.nM, s.nN, s.nK, false), rows_splits(s.nH, s.nM, s.nN, s.nK)});
+    if (use_dot(s.nM, s.nN, s.nK)) sp = std::max(sp, dot_splits(s.nH, s.nM, s.nN, s.nK));
+    if (sp > 1 || use_dot(s.nM, s.nN, s.nK))
+      max_part = std::max(max_part, size_t(sp) * 8 * (size_t(1) << (s.nH + s.nM + s.nN)));
+  }
+  p->ws_partial = off;
+  off = align_up(off + max_part + 256, 1024);
   p->ws_acc = off;
   off = align_up(off + 16 * (size_t(1) << p->tensors[p->root].rank), 256);
   p->ws_misc = off;
@@ -182,29 +196,68 @@ tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) {
     cands.push_back(greedy_tree(h, {}, o.seed, 0.0));
   if (mode == TNQ_PATH_BISECT || mode == TNQ_PATH_BEST || mode == TNQ_PATH_LEARNED) {
     std::mt19937_64 g(o.seed ^ 0x5bd1e995ULL);
+    struct Spec {
+      uint64_t seed;
+      double imb;
+      int grp;
+    };
+    std::vector<Spec> specs(nc);
     for (int i = 0; i < nc; ++i) {
-      double imb = 0.05 + 0.6 * ((g() >> 11) * (1.0 / 9007199254740992.0));
-      int grp = 4 + int(g() % 12);
-      cands.push_back(bisect_tree(h, g(), imb, grp));
+      specs[i].imb = 0.05 + 0.6 * ((g() >> 11) * (1.0 / 9007199254740992.0));
+      specs[i].grp = 4 + int(g() % 12);
+      specs[i].seed = g();
     }
+    size_t base = cands.size();
+    cands.resize(base + nc);
+    int nthreads = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 32u);
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < std::min(nthreads, nc); ++t)
+      pool.emplace_back([&] {
+        for (int i = next++; i < nc; i = next++) cands[base + i] = bisect_tree(h, specs[i].seed, specs[i].imb, specs[i].grp);
+      });
+    for (auto& th : pool) th.join();
     for (int i = 0; i < nc / 4; ++i) cands.push_back(greedy_tree(h, {}, g(), 0.3 + 0.2 * (i % 4)));
   }
   if (cands.empty()) return fail(TNQ_ERR_INVALID_ARG, "unknown path_mode");
-  double best_total = 0;
-  int best = -1;
-  std::vector<int> best_slices;
-  for (int i = 0; i < (int)cands.size(); ++i) {
+  // Evaluate candidates (slicing included) on host threads; each candidate's
+  // result depends only on its own seed, and ties go to the lowest index, so
+  // the choice is deterministic.
+  const int NC = (int)cands.size();
+  std::vector<double> totals(NC, -1.0);
+  std::vector<std::vector<int>> slices(NC);
+  auto eval = [&](int i) {
     bool feas = false;
     std::vector<int> sl = choose_slices(h, cands[i], o.max_intermediate_log2, &feas);
-    if (!feas) continue;
+    if (!feas) return;
     std::vector<char> sv(h.n_labels, 0);
     for (int l : sl) sv[l] = 1;
     TreeCost tc = tree_cost(h, cands[i], sv);
-    double total = tc.flops * std::ldexp(1.0, (int)sl.size());
-    if (best < 0 || total < best_total) {
+    totals[i] = tc.flops * std::ldexp(1.0, (int)sl.size());
+    slices[i] = sl;
+  };
+  int nthreads = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 32u);
+  nthreads = std::min(nthreads, NC);
+  if (nthreads <= 1) {
+    for (int i = 0; i < NC; ++i) eval(i);
+  } else {
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+      pool.emplace_back([&] {
+        for (int i = next++; i < NC; i = next++) eval(i);
+      });
+    for (auto& th : pool) th.join();
+  }
+  double best_total = 0;
+  int best = -1;
+  std::vector<int> best_slices;
+  for (int i = 0; i < NC; ++i) {
+    if (totals[i] < 0) continue;
+    if (best < 0 || totals[i] < best_total) {
       best = i;
-      best_total = total;
-      best_slices = sl;
+      best_total = totals[i];
+      best_slices = slices[i];
     }
   }
   if (best < 0)

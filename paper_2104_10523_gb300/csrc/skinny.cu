@@ -1,0 +1,201 @@
+// Bandwidth-oriented complex GEMMs for skinny contraction steps.
+//
+// Many steps of a contraction path have a tiny side: few output rows (a small
+// operand meeting a large one) or a tiny output with a long contracted
+// dimension (the inner products that close a network).  Their cost is reading
+// the large operand once; a tiled GEMM would leave most lanes idle.
+//
+//   rows kernel:  C[h][s][g] = sum_k S[h][s][k] G[h][g][k] for a small side of
+//                 at most 16 rows: each thread owns one row g of the large
+//                 operand, the small operand and a K slice of G are staged in
+//                 shared memory by coalesced loads; output strides make the
+//                 same kernel serve both "small M" and "small N".
+//   dot kernel:   M, N <= 4 and long K: every thread walks its own part of K
+//                 with 16-byte loads and keeps the M x N sums in registers; the
+//                 CTA reduces them and writes one partial per CTA.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace tnq {
+
+namespace {
+
+constexpr int RW_THREADS = 128;  // rows of the large operand per CTA
+constexpr int RW_KC = 32;        // K elements staged per iteration
+constexpr int RW_SMAX = 16;
+
+__global__ void __launch_bounds__(RW_THREADS) cgemm_rows_kernel(
+    const float2* __restrict__ S, const float2* __restrict__ G, float2* __restrict__ C, double2* __restrict__ acc,
+    float2* __restrict__ part, int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
+    int kchunk, int tiles_g) {
+  __shared__ float2 Gs[RW_THREADS][RW_KC + 1];
+  __shared__ float2 Ss[RW_SMAX][RW_KC + 1];
+  const int t = threadIdx.x;
+  const int tile = int(blockIdx.x % tiles_g);
+  const int h = int(blockIdx.x / tiles_g);
+  const int g0 = tile * RW_THREADS;
+  const int split = blockIdx.y;
+  const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
+  const float2* Sh = S + size_t(h) * ns * K;
+  const float2* Gh = G + size_t(h) * ng * K;
+  float ar[RW_SMAX], ai[RW_SMAX];
+#pragma unroll
+  for (int s = 0; s < RW_SMAX; ++s) ar[s] = ai[s] = 0.f;
+  for (int k0 = kbeg; k0 < kend; k0 += RW_KC) {
+    const int kc = min(RW_KC, kend - k0);
+    // stage G[g0 .. g0+127][k0 .. k0+kc): row segments are contiguous in K
+    for (int idx = t; idx < RW_THREADS * RW_KC; idx += RW_THREADS) {
+      const int r = idx / RW_KC, kk = idx % RW_KC;
+      float2 v = make_float2(0.f, 0.f);
+      if (g0 + r < ng && kk < kc) v = Gh[size_t(g0 + r) * K + k0 + kk];
+      Gs[r][kk] = v;
+    }
+    for (int idx = t; idx < RW_SMAX * RW_KC; idx += RW_THREADS) {
+      const int r = idx / RW_KC, kk = idx % RW_KC;
+      float2 v = make_float2(0.f, 0.f);
+      if (r < ns && kk < kc) v = Sh[size_t(r) * K + k0 + kk];
+      Ss[r][kk] = v;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const float2 g = Gs[t][kk];
+#pragma unroll
+      for (int s = 0; s < RW_SMAX; ++s) {
+        if (s < ns) {
+          const float2 a = Ss[s][kk];
+          ar[s] = fmaf(a.x, g.x, ar[s]);
+          ar[s] = fmaf(-a.y, g.y, ar[s]);
+          ai[s] = fmaf(a.x, g.y, ai[s]);
+          ai[s] = fmaf(a.y, g.x, ai[s]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int g = g0 + t;
+  if (g >= ng) return;
+  const size_t hbase = size_t(h) * ns * ng;
+#pragma unroll
+  for (int s = 0; s < RW_SMAX; ++s) {
+    if (s < ns) {
+      const size_t o = hbase + size_t(s) * s_stride_out + size_t(g) * g_stride_out;
+      if (part) {
+        part[size_t(split) * batch * ns * ng + o] = make_float2(ar[s], ai[s]);
+      } else if (acc) {
+        double2 v = acc[o];
+        v.x += ar[s];
+        v.y += ai[s];
+        acc[o] = v;
+      } else {
+        C[o] = make_float2(ar[s], ai[s]);
+      }
+    }
+  }
+}
+
+constexpr int DOT_THREADS = 256;
+
+__global__ void __launch_bounds__(DOT_THREADS) cdot_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                           float2* __restrict__ part, int M, int N, int K,
+                                                           int kchunk, int splits) {
+  __shared__ float red[DOT_THREADS / 32][32];
+  const int split = blockIdx.x, h = blockIdx.y;
+  const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
+  const float2* Ah = A + size_t(h) * M * K;
+  const float2* Bh = B + size_t(h) * N * K;
+  float cr[4][4], ci[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cr[i][j] = ci[i][j] = 0.f;
+  // two complex values per 16-byte load (kbeg is even because kchunk is)
+  for (int k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * DOT_THREADS) {
+    const bool two = k + 1 < kend;
+    float4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      b[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < M) {
+        if (two) a[i] = *reinterpret_cast<const float4*>(Ah + size_t(i) * K + k);
+        else { float2 v = Ah[size_t(i) * K + k]; a[i].x = v.x; a[i].y = v.y; }
+      }
+      if (i < N) {
+        if (two) b[i] = *reinterpret_cast<const float4*>(Bh + size_t(i) * K + k);
+        else { float2 v = Bh[size_t(i) * K + k]; b[i].x = v.x; b[i].y = v.y; }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
+        cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
+        ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
+        ci[i][j] = fmaf(a[i].y, b[j].x, ci[i][j]);
+        cr[i][j] = fmaf(a[i].z, b[j].z, cr[i][j]);
+        cr[i][j] = fmaf(-a[i].w, b[j].w, cr[i][j]);
+        ci[i][j] = fmaf(a[i].z, b[j].w, ci[i][j]);
+        ci[i][j] = fmaf(a[i].w, b[j].z, ci[i][j]);
+      }
+  }
+  // reduce the 32 sums (16 re, 16 im) over the CTA in a fixed order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float r = cr[i][j], im = ci[i][j];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        r += __shfl_xor_sync(0xffffffffu, r, off);
+        im += __shfl_xor_sync(0xffffffffu, im, off);
+      }
+      if (lane == 0) {
+        red[warp][2 * (i * 4 + j)] = r;
+        red[warp][2 * (i * 4 + j) + 1] = im;
+      }
+    }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = 0.f;
+    for (int w = 0; w < DOT_THREADS / 32; ++w) v += red[w][threadIdx.x];
+    const int ij = threadIdx.x >> 1, i = ij >> 2, j = ij & 3;
+    if (i < M && j < N) {
+      float* dst = reinterpret_cast<float*>(part + (size_t(split) * gridDim.y + h) * M * N + size_t(i) * N + j);
+      dst[threadIdx.x & 1] = v;
+    }
+  }
+  (void)splits;
+}
+
+}  // namespace
+
+cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, void* acc, void* part, int splits,
+                              int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
+                              cudaStream_t st) {
+  if (ns < 1 || ns > RW_SMAX || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
+  const long long tiles_g = (ng + RW_THREADS - 1) / RW_THREADS;
+  if (tiles_g * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  int kchunk = ((K + splits - 1) / splits + RW_KC - 1) / RW_KC * RW_KC;
+  dim3 grid{unsigned(tiles_g * batch), unsigned(splits), 1u};
+  cgemm_rows_kernel<<<grid, RW_THREADS, 0, st>>>(
+      reinterpret_cast<const float2*>(Ssmall), reinterpret_cast<const float2*>(Gbig), reinterpret_cast<float2*>(C),
+      reinterpret_cast<double2*>(acc), splits > 1 ? reinterpret_cast<float2*>(part) : nullptr, ns, ng, K, batch,
+      s_stride_out, g_stride_out, kchunk, int(tiles_g));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, int M, int N, int K, int batch,
+                        cudaStream_t st) {
+  if (M < 1 || M > 4 || N < 1 || N > 4 || splits < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + 1) & ~1;
+  dim3 grid{unsigned(splits), unsigned(batch), 1u};
+  cdot_kernel<<<grid, DOT_THREADS, 0, st>>>(reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(B),
+                                            reinterpret_cast<float2*>(part), M, N, K, kchunk, splits);
+  return cudaGetLastError();
+}
+
+}  // namespace tnq

@@ -34,6 +34,7 @@ EXPORTS = (
     "tnq_plan_get_steps", "tnq_ctx_create", "tnq_ctx_destroy", "tnq_ctx_set_precision",
     "tnq_plan_bind", "tnq_amplitudes", "tnq_noisy_probabilities",
     "tnq_contract_workspace_bytes", "tnq_contract_pair",
+    "tnq_ctx_launch_count", "tnq_ctx_set_timing", "tnq_ctx_get_timings",
 )
 
 
@@ -97,6 +98,9 @@ def load() -> C.CDLL:
         "tnq_noisy_probabilities": ([vp, vp, i64, u64, i64, vp, vp, vp], i32),
         "tnq_contract_workspace_bytes": ([i32, i32, i32, i32], sz),
         "tnq_contract_pair": ([vp, vp, i32, ip, vp, i32, ip, vp, i32, ip, vp, sz], i32),
+        "tnq_ctx_launch_count": ([vp, C.POINTER(C.c_uint64)], i32),
+        "tnq_ctx_set_timing": ([vp, i32], i32),
+        "tnq_ctx_get_timings": ([vp, dp, i32, ip], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -213,6 +217,28 @@ def tnq_contract_pair(ctx, A, a_labels, B, b_labels, Cout, c_labels, workspace, 
     check(load().tnq_contract_pair(ctx, _ptr(A), len(a_labels), _int_array(a_labels), _ptr(B), len(b_labels),
                                    _int_array(b_labels), _ptr(Cout), len(c_labels), _int_array(c_labels),
                                    _ptr(workspace), int(nbytes)))
+
+
+def tnq_ctx_launch_count(ctx) -> int:
+    v = C.c_uint64()
+    check(load().tnq_ctx_launch_count(ctx, C.byref(v)))
+    return int(v.value)
+
+
+def tnq_ctx_set_timing(ctx, enable: bool):
+    check(load().tnq_ctx_set_timing(ctx, 1 if enable else 0))
+
+
+TIMING_FIELDS = ("kind", "step", "log2_h", "log2_m", "log2_n", "log2_k", "flops", "bytes", "ms", "pad")
+
+
+def tnq_ctx_get_timings(ctx) -> np.ndarray:
+    """Per-kernel records [n][10] (see TIMING_FIELDS)."""
+    n = C.c_int()
+    check(load().tnq_ctx_get_timings(ctx, None, 0, C.byref(n)))
+    rec = np.zeros((max(n.value, 1), 10), dtype=np.float64)
+    check(load().tnq_ctx_get_timings(ctx, rec.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
+    return rec[:n.value]
 
 
 # ---------------------------------------------------------------- owning helpers

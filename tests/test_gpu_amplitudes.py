@@ -53,6 +53,18 @@ def test_config_small_fp32(T, small_ref, w, mode):
     assert rel_l2(amp, ref) <= TOL["fp32"]
 
 
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16x3"])
+def test_config_small_tensor_core_modes(T, small_ref, prec):
+    c, ref = small_ref
+    ctx = T.Context(0, prec)
+    ctx_set = ctx  # the small steps of this circuit would all stay on the CUDA cores; force the tensor cores
+    plan = T.Plan(T.Circuit(c), batch_log2=6, path_mode=2, n_candidates=4, seed=1)
+    ctx.bind(plan)
+    T.tnq_ctx_set_timing(ctx_set.h, True)
+    amp = ctx.amplitudes(plan, CONFIG_SMALL_BITS)
+    assert rel_l2(amp, ref) <= TOL[prec]
+
+
 def test_config_small_matches_tn_oracle(T, small_ref):
     c, _ = small_ref
     ref2 = otn.amplitudes(c, CONFIG_SMALL_BITS[:16])

@@ -1,0 +1,92 @@
+"""GPU parity of one pairwise contraction (permute + complex GEMM) in every
+precision mode against the FP64 oracle (oracle.contraction).
+
+Operands are the seeded microbenchmark pairs (all index dimensions 2, shared
+indices scattered by a seeded permutation, entries complex normal / sqrt(K)).
+Small cases compare every output entry; large ones compare sampled output rows
+that the oracle computes one by one.  Shapes with a tiny output and a long
+contracted dimension exercise the split-K path (FP32 partials, ordered sum).  Bound on the relative L2 error per mode
+for a single contraction: FP32 and TF32x3 1e-5, BF16x3 2e-5, TF32 5e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import contraction
+from workloads import microbench_case
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 2e-5, "tf32": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2104_10523_gb300 import build, tnq
+    build.build()
+    tnq.load()
+    return tnq
+
+
+def _run(T, prec, A, al, B, bl, ol):
+    import torch
+    ctx = T.Context(0, prec)
+    At = torch.from_numpy(A).cuda()
+    Bt = torch.from_numpy(B).cuda()
+    Ct = torch.full((2 ** len(ol),), float("nan"), dtype=torch.complex64, device="cuda")
+    nb = T.tnq_contract_workspace_bytes(T.PRECISIONS[prec], len(al), len(bl), len(ol))
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    T.tnq_contract_pair(ctx.h, At, al, Bt, bl, Ct, ol, ws, nb)
+    torch.cuda.synchronize()
+    return Ct.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("mnk", [(2, 3, 4), (6, 6, 6), (7, 5, 8), (3, 9, 10), (8, 8, 2), (6, 8, 10),
+                                 (2, 2, 18), (0, 1, 16), (5, 6, 14), (9, 4, 12)])
+def test_full_output(T, prec, mnk):
+    m, n, k = mnk
+    al, bl, ol, A, B = microbench_case(m, n, k, seed=m * 100 + n * 10 + k)
+    C = _run(T, prec, A, al, B, bl, ol)
+    ref = contraction.contract_labeled(A, al, B, bl, ol)
+    assert np.all(np.isfinite(C))
+    assert rel(C, ref) <= TOL[prec], (prec, mnk, rel(C, ref))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("mnk", [(10, 10, 12), (12, 8, 14), (8, 14, 8)])
+def test_sampled_rows(T, prec, mnk):
+    m, n, k = mnk
+    al, bl, ol, A, B = microbench_case(m, n, k, seed=7 + m + n + k)
+    C = _run(T, prec, A, al, B, bl, ol)
+    rows = np.random.default_rng(1).choice(2 ** m, size=16, replace=False)
+    ref = contraction.sampled_rows(A, al, B, bl, ol, rows, ol[:m])
+    got = C.reshape(2 ** n, 2 ** m).T[rows]
+    assert rel(got, ref) <= TOL[prec], (prec, mnk, rel(got, ref))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_batch_labels(T, prec):
+    """Labels held by A, B and C are batch indices (the batched-GEMM case)."""
+    rng = np.random.default_rng(5)
+    al = [0, 1, 2, 3, 4, 5, 6, 7, 20, 21]         # 20, 21: batch; 4..7 contracted
+    bl = [21, 4, 5, 6, 7, 8, 9, 10, 11, 20]
+    ol = [8, 0, 9, 1, 20, 2, 10, 3, 11, 21]
+    A = (rng.standard_normal(2 ** 10) + 1j * rng.standard_normal(2 ** 10)).astype(np.complex64)
+    B = (rng.standard_normal(2 ** 10) + 1j * rng.standard_normal(2 ** 10)).astype(np.complex64)
+    C = _run(T, prec, A, al, B, bl, ol)
+    ref = contraction.contract_labeled(A, al, B, bl, ol)
+    assert rel(C, ref) <= TOL[prec]
+
+
+def test_invalid_labels_rejected(T):
+    import torch
+    ctx = T.Context(0, "fp32")
+    A = torch.zeros(4, dtype=torch.complex64, device="cuda")
+    ws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(T.TnqError) as e:
+        T.tnq_contract_pair(ctx.h, A, [0, 1], A, [1, 2], A, [0, 5], ws, 1 << 16)
+    assert e.value.status == T.TNQ_ERR_INVALID_ARG

@@ -237,6 +237,14 @@ def test_contraction_matches_loop_brute_force():
         val = dict(enumerate(v))
         ref[idx(out_labels, val)] += A[idx(a_labels, val)] * B[idx(b_labels, val)]
     assert np.allclose(C, ref, atol=1e-14)
+    # a label held by A, B and the output is a batch index
+    a2, b2, o2 = [3, 0, 5, 1], [5, 2, 3], [1, 5, 2, 0]
+    C2 = contraction.contract_labeled(A, a2, B, b2, o2)
+    ref2 = np.zeros(16, dtype=np.complex128)
+    for v in itertools.product((0, 1), repeat=5):
+        val = dict(zip([0, 1, 2, 3, 5], v))
+        ref2[idx(o2, val)] += A[idx(a2, val)] * B[idx(b2, val)]
+    assert np.allclose(C2, ref2, atol=1e-14)
     rows = contraction.sampled_rows(A, a_labels, B, b_labels, out_labels, rows=[0, 3],
                                     row_labels=[0, 1])
     for i, r in enumerate([0, 3]):
