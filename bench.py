@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--cap", type=int, default=28)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="circuit", choices=["circuit", "pair"],
+                    help="circuit: 6x6 amplitude workload; pair: one pairwise contraction (microbenchmark)")
+    ap.add_argument("--mnk", default="12,12,12", help="pair workload: log2 of M, N, K")
     return ap.parse_args()
 
 
@@ -162,6 +165,8 @@ def main():
 
     if a.impl == "reference":
         return run_reference(a, world, rank)
+    if a.workload == "pair":
+        return run_pair(a, local, rank)
 
     import numpy as np
     import torch
@@ -372,6 +377,59 @@ def load_traffic(kernel):
     except OSError:
         return None
     return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+def run_pair(a, local, rank):
+    """Pairwise-contraction microbenchmark: all-dimension-2 complex64 operands of
+    rank m+k and n+k with the shared indices scattered by a seeded permutation
+    (entries complex normal / sqrt(2^k)); one step = one tnq_contract_pair call
+    (operand permutes + complex GEMM + output permute).  Error against the FP64
+    oracle on 16 sampled output rows."""
+    import numpy as np
+    import torch
+    from oracle import contraction
+    from paper_2104_10523_gb300 import build, tnq
+    from workloads import microbench_case
+    m, n, k = (int(x) for x in a.mnk.split(","))
+    torch.cuda.set_device(local)
+    build.build()
+    tnq.load()
+    al, bl, ol, A, B = microbench_case(m, n, k, seed=1)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = torch.empty(2 ** (m + n), dtype=torch.complex64, device="cuda")
+    ctx = tnq.Context(local, a.precision)
+    nb = tnq.tnq_contract_workspace_bytes(tnq.PRECISIONS[a.precision], len(al), len(bl), len(ol))
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+
+    def step():
+        tnq.tnq_contract_pair(ctx.h, At, al, Bt, bl, C, ol, ws, nb)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / a.steps
+    tnq.tnq_ctx_set_timing(ctx.h, True)
+    step()
+    rec = tnq.tnq_ctx_get_timings(ctx.h)
+    roofline, share = roofline_of(rec, a.precision)
+    rows = np.random.default_rng(1).choice(2 ** m, size=16, replace=False)
+    ref = contraction.sampled_rows(A, al, B, bl, ol, rows, ol[:m])
+    got = C.cpu().numpy().reshape(2 ** n, 2 ** m).T[rows]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    flops = 8.0 * 2.0 ** (m + n + k)
+    line = {"metric": "contraction TFLOP/s", "value": flops / dt / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
+            "config": {"workload": f"pairwise contraction M=2^{m} N=2^{n} K=2^{k}, complex64 all-dim-2 tensors"},
+            "rel_l2_vs_fp64": err, "roofline": roofline, "kernel_share": share}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_reference(a, world, rank):
