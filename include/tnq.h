@@ -186,6 +186,22 @@ tnq_status tnq_contract_pair(tnq_ctx* ctx, const void* A, int ra, const int* a_l
                              const void* B, int rb, const int* b_labels, void* C, int rc,
                              const int* c_labels, void* workspace, size_t workspace_bytes);
 
+/* Pairwise contraction that allocates no device memory (the paper has no
+ * counterpart).  Same operation, arguments and precision handling as
+ * tnq_contract_pair, without the workspace: for callers that may not allocate
+ * device memory while they run, such as programs whose own pool allocator owns
+ * all device memory, or latency-critical loops that cannot accept the device
+ * synchronisation that freeing memory implies.  Its scratch is one static
+ * device array of 64 MiB inside the library, held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's address and should come before any stream capture.  All calls share
+ * the array and it keeps the last call's contents, so calls that overlap on
+ * the GPU race.  Errors: INVALID_ARG when the contraction needs more than 64 MiB
+ * of scratch (see tnq_contract_workspace_bytes) or the labels are inconsistent;
+ * TIMEOUT, CUDA as tnq_contract_pair. */
+tnq_status tnq_contract_pair_noalloc(tnq_ctx* ctx, const void* A, int ra, const int* a_labels, const void* B,
+                                     int rb, const int* b_labels, void* C, int rc, const int* c_labels);
+
 /* ---- measurement ---------------------------------------------------------- */
 /* Number of kernels this context has launched so far (cumulative). */
 tnq_status tnq_ctx_launch_count(const tnq_ctx* ctx, uint64_t* count);

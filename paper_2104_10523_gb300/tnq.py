@@ -35,6 +35,7 @@ EXPORTS = (
     "tnq_plan_bind", "tnq_amplitudes", "tnq_noisy_probabilities",
     "tnq_contract_workspace_bytes", "tnq_contract_pair",
     "tnq_ctx_launch_count", "tnq_ctx_set_timing", "tnq_ctx_get_timings",
+    "tnq_contract_pair_noalloc",
 )
 
 
@@ -101,6 +102,7 @@ def load() -> C.CDLL:
         "tnq_ctx_launch_count": ([vp, C.POINTER(C.c_uint64)], i32),
         "tnq_ctx_set_timing": ([vp, i32], i32),
         "tnq_ctx_get_timings": ([vp, dp, i32, ip], i32),
+        "tnq_contract_pair_noalloc": ([vp, vp, i32, ip, vp, i32, ip, vp, i32, ip], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -217,6 +219,13 @@ def tnq_contract_pair(ctx, A, a_labels, B, b_labels, Cout, c_labels, workspace, 
     check(load().tnq_contract_pair(ctx, _ptr(A), len(a_labels), _int_array(a_labels), _ptr(B), len(b_labels),
                                    _int_array(b_labels), _ptr(Cout), len(c_labels), _int_array(c_labels),
                                    _ptr(workspace), int(nbytes)))
+
+
+def tnq_contract_pair_noalloc(ctx, A, a_labels, B, b_labels, Cout, c_labels):
+    """tnq_contract_pair without a workspace argument (scratch is static in the library)."""
+    check(load().tnq_contract_pair_noalloc(ctx, _ptr(A), len(a_labels), _int_array(a_labels), _ptr(B),
+                                           len(b_labels), _int_array(b_labels), _ptr(Cout), len(c_labels),
+                                           _int_array(c_labels)))
 
 
 def tnq_ctx_launch_count(ctx) -> int:
