@@ -174,6 +174,14 @@ tnq_status tnq_noisy_probabilities(tnq_ctx* ctx, tnq_plan* p, int64_t n_traj, ui
                                    int64_t n_bs, const int8_t* bits, double* p_out,
                                    double* stderr_out);
 
+/* Amplitudes of individual trajectories (the unnormalised <x|psi_t> whose
+ * squared moduli tnq_noisy_probabilities averages): trajectories
+ * traj_begin .. traj_begin + n_traj - 1 with the same draws as above.
+ * out: [n_traj][n_bs][2] double (re, im), host or device.  Errors as
+ * tnq_noisy_probabilities. */
+tnq_status tnq_trajectory_amplitudes(tnq_ctx* ctx, tnq_plan* p, uint64_t seed, int64_t traj_begin,
+                                     int64_t n_traj, int64_t n_bs, const int8_t* bits, double* out);
+
 /* One pairwise contraction (a single step of Sec. 3.1's sequence) of device
  * tensors A (rank ra, labels a_labels) and B (rank rb, labels b_labels) into
  * C (rank rc, labels c_labels): C = sum over the labels A and B share but C

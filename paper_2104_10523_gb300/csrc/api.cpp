@@ -242,6 +242,12 @@ tnq_status tnq_noisy_probabilities(tnq_ctx* c, tnq_plan* p, int64_t n_traj, uint
   return exec_noisy(&c->c, &p->p, n_traj, seed, n_bs, bits, p_out, se_out);
 }
 
+tnq_status tnq_trajectory_amplitudes(tnq_ctx* c, tnq_plan* p, uint64_t seed, int64_t traj_begin, int64_t n_traj,
+                                     int64_t n_bs, const int8_t* bits, double* out) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return exec_traj_amplitudes(&c->c, &p->p, seed, traj_begin, n_traj, n_bs, bits, out);
+}
+
 size_t tnq_contract_workspace_bytes(int precision, int ra, int rb, int rc) {
   if (ra < 0 || rb < 0 || rc < 0 || ra > 31 || rb > 31 || rc > 31) return 0;
   return contract_workspace_bytes(precision, ra, rb, rc);

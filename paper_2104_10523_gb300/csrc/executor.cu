@@ -295,6 +295,23 @@ tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes) {
                              cudaMemcpyHostToDevice, ctx->stream));
     TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
   }
+  if (!p->traj_leaves.empty()) {
+    std::vector<double> mats(2 * p->traj_mats.size());
+    for (size_t k = 0; k < p->traj_mats.size(); ++k) {
+      mats[2 * k] = p->traj_mats[k].real();
+      mats[2 * k + 1] = p->traj_mats[k].imag();
+    }
+    TNQ_CUDA(cudaMemcpyAsync(base + p->ws_traj, p->traj_leaves.data(), sizeof(TrajLeafDesc) * p->traj_leaves.size(),
+                             cudaMemcpyHostToDevice, ctx->stream));
+    TNQ_CUDA(cudaMemcpyAsync(base + p->ws_traj_factors, p->traj_factors.data(),
+                             sizeof(TrajFactor) * p->traj_factors.size(), cudaMemcpyHostToDevice, ctx->stream));
+    TNQ_CUDA(cudaMemcpyAsync(base + p->ws_traj_mats, mats.data(), 8 * mats.size(), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    if (!p->traj_cumq.empty())
+      TNQ_CUDA(cudaMemcpyAsync(base + p->ws_traj_cumq, p->traj_cumq.data(), 8 * p->traj_cumq.size(),
+                               cudaMemcpyHostToDevice, ctx->stream));
+    TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
   p->bound_ws = ws;
   p->bound_bytes = bytes;
   return TNQ_OK;
@@ -314,8 +331,8 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
     for (int64_t i = 0; i < n_bs * n; ++i)
       if (bits[i] != 0 && bits[i] != 1) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
   int* err_flag = reinterpret_cast<int*>(ws + p->ws_misc);
-  int8_t* bits_stage = reinterpret_cast<int8_t*>(ws + p->ws_misc + 256);
-  double* out_stage = reinterpret_cast<double*>(ws + p->ws_misc + 256 + ((size_t(n) * per + 255) / 256) * 256);
+  int8_t* bits_stage = reinterpret_cast<int8_t*>(ws + p->ws_bits);
+  double* out_stage = reinterpret_cast<double*>(ws + p->ws_out_stage);
   const int L = p->tree.n_leaves;
   int first_proj = -1;
   for (int i = 0; i < L; ++i)
@@ -365,17 +382,163 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
   return TNQ_OK;
 }
 
+namespace {
+
+// Shared driver of the noisy calls: for every batch of bitstrings and every
+// chunk of 2^traj_log2 trajectories, build the trajectory leaves, contract all
+// slices into the FP64 accumulator, then hand the accumulator to `consume`.
+template <typename Consume, typename BatchEnd>
+tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, uint64_t seed, int64_t n_bs,
+                        const int8_t* bits, Consume consume, BatchEnd batch_end) {
+  char* ws = static_cast<char*>(p->bound_ws);
+  const int n = p->net.n_qubits, w = p->batch_log2, t = p->traj_log2;
+  const int64_t per = int64_t(1) << w, tper = int64_t(1) << t;
+  const bool bits_dev = is_device_ptr(bits);
+  if (!bits_dev)
+    for (int64_t i = 0; i < n_bs * n; ++i)
+      if (bits[i] != 0 && bits[i] != 1) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  int* err_flag = reinterpret_cast<int*>(ws + p->ws_misc);
+  int8_t* bits_stage = reinterpret_cast<int8_t*>(ws + p->ws_bits);
+  const int L = p->tree.n_leaves;
+  int first_proj = -1;
+  for (int i = 0; i < L; ++i)
+    if (p->net.leaves[i].kind == LEAF_PROJ) {
+      first_proj = i;
+      break;
+    }
+  size_t stride = first_proj + 1 < L ? p->tensors[first_proj + 1].offset - p->tensors[first_proj].offset : 0;
+  const auto& rl = p->tensors[p->root].labels;
+  std::vector<int> bpos(w), tpos(t);
+  for (int j = 0; j < w; ++j) bpos[j] = int(std::find(rl.begin(), rl.end(), p->net.batch_labels[j]) - rl.begin());
+  for (int j = 0; j < t; ++j) tpos[j] = int(std::find(rl.begin(), rl.end(), p->net.traj_labels[j]) - rl.begin());
+  TNQ_CUDA(cudaMemsetAsync(err_flag, 0, 2 * sizeof(int), ctx->stream));
+  const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
+  const int n_slices = 1 << p->slice_labels.size();
+  for (int64_t base = 0; base < n_bs; base += per) {
+    const int64_t nv = std::min<int64_t>(per, n_bs - base);
+    const int8_t* bsrc;
+    if (bits_dev) {
+      bsrc = bits + base * n;
+    } else {
+      TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * n, size_t(nv) * n, cudaMemcpyHostToDevice, ctx->stream));
+      bsrc = bits_stage;
+    }
+    TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w, bsrc, nv, err_flag, ctx->stream));
+    ctx->launches++;
+    tnq_status st = consume(-1, base, nv, 0, 0, bpos, tpos);  // batch start
+    if (st != TNQ_OK) return st;
+    for (int64_t tb = 0; tb < n_traj; tb += tper) {
+      const int64_t nt = std::min<int64_t>(tper, n_traj - tb);
+      TNQ_CUDA(launch_traj_leaves(reinterpret_cast<const TrajLeafDesc*>(ws + p->ws_traj), (int)p->traj_leaves.size(),
+                                  reinterpret_cast<const TrajFactor*>(ws + p->ws_traj_factors),
+                                  reinterpret_cast<const double2*>(ws + p->ws_traj_mats),
+                                  reinterpret_cast<const double*>(ws + p->ws_traj_cumq), ws, seed,
+                                  uint64_t(traj_begin + tb), t, ctx->stream));
+      ctx->launches++;
+      TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
+      for (int s = 0; s < n_slices; ++s) {
+        st = run_pass(ctx, p, s, ws);
+        if (st != TNQ_OK) return st;
+      }
+      st = consume(0, base, nv, tb, nt, bpos, tpos);
+      if (st != TNQ_OK) return st;
+    }
+    st = batch_end(base, nv);
+    if (st != TNQ_OK) return st;
+  }
+  int herr[2] = {0, 0};
+  TNQ_CUDA(cudaMemcpyAsync(herr, err_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->timing) {
+    tnq_status ts = timing_collect(ctx);
+    if (ts != TNQ_OK) return ts;
+  }
+  if (herr[1]) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired; results are invalid");
+  if (herr[0]) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  return TNQ_OK;
+}
+
+tnq_status noisy_checks(Plan* p, int64_t n_traj, int64_t n_bs, const int8_t* bits, const void* out) {
+  if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
+  if (!p->net.noisy) return fail(TNQ_ERR_INVALID_ARG, "plan is for a circuit without channels");
+  if (n_traj < 1) return fail(TNQ_ERR_INVALID_ARG, "n_traj must be >= 1");
+  if (n_bs < 0 || (n_bs > 0 && (!bits || !out))) return fail(TNQ_ERR_INVALID_ARG, "bad bitstring/output buffers");
+  return TNQ_OK;
+}
+
+}  // namespace
+
 tnq_status exec_noisy(Ctx* ctx, Plan* p, int64_t n_traj, uint64_t seed, int64_t n_bs, const int8_t* bits,
                       double* p_out, double* se_out) {
-  (void)ctx;
-  (void)p;
-  (void)n_traj;
-  (void)seed;
-  (void)n_bs;
-  (void)bits;
-  (void)p_out;
-  (void)se_out;
-  return fail(TNQ_ERR_NOT_SUPPORTED, "noisy trajectories not built yet");
+  tnq_status st = noisy_checks(p, n_traj, n_bs, bits, p_out);
+  if (st != TNQ_OK || n_bs == 0) return st;
+  TNQ_CUDA(cudaSetDevice(ctx->device));
+  char* ws = static_cast<char*>(p->bound_ws);
+  double* psum = reinterpret_cast<double*>(ws + p->ws_psum);
+  double* p2sum = reinterpret_cast<double*>(ws + p->ws_p2sum);
+  double* stage = reinterpret_cast<double*>(ws + p->ws_out_stage);
+  const int64_t per = int64_t(1) << p->batch_log2;
+  const bool p_dev = is_device_ptr(p_out), se_dev = se_out && is_device_ptr(se_out);
+  auto consume = [&](int phase, int64_t, int64_t nv, int64_t, int64_t nt, const std::vector<int>& bpos,
+                     const std::vector<int>& tpos) -> tnq_status {
+    if (phase < 0) {
+      TNQ_CUDA(cudaMemsetAsync(psum, 0, 8 * per, ctx->stream));
+      TNQ_CUDA(cudaMemsetAsync(p2sum, 0, 8 * per, ctx->stream));
+      return TNQ_OK;
+    }
+    TNQ_CUDA(launch_noisy_accumulate(ws + p->ws_acc, nv, nt, bpos.data(), (int)bpos.size(), tpos.data(),
+                                     (int)tpos.size(), psum, p2sum, ctx->stream));
+    ctx->launches++;
+    return TNQ_OK;
+  };
+  auto batch_end = [&](int64_t base, int64_t nv) -> tnq_status {
+    double* pd = p_dev ? p_out + base : stage;
+    double* sd = se_out ? (se_dev ? se_out + base : stage + per) : nullptr;
+    TNQ_CUDA(launch_noisy_finalize(psum, p2sum, nv, n_traj, pd, sd, ctx->stream));
+    ctx->launches++;
+    if (!p_dev) TNQ_CUDA(cudaMemcpyAsync(p_out + base, stage, 8 * nv, cudaMemcpyDeviceToHost, ctx->stream));
+    if (se_out && !se_dev)
+      TNQ_CUDA(cudaMemcpyAsync(se_out + base, stage + per, 8 * nv, cudaMemcpyDeviceToHost, ctx->stream));
+    if (!p_dev || (se_out && !se_dev)) TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return TNQ_OK;
+  };
+  return noisy_driver(ctx, p, 0, n_traj, seed, n_bs, bits, consume, batch_end);
+}
+
+tnq_status exec_traj_amplitudes(Ctx* ctx, Plan* p, uint64_t seed, int64_t traj_begin, int64_t n_traj, int64_t n_bs,
+                                const int8_t* bits, double* out) {
+  tnq_status st = noisy_checks(p, n_traj, n_bs, bits, out);
+  if (st != TNQ_OK || n_bs == 0) return st;
+  if (traj_begin < 0) return fail(TNQ_ERR_INVALID_ARG, "traj_begin must be >= 0");
+  TNQ_CUDA(cudaSetDevice(ctx->device));
+  char* ws = static_cast<char*>(p->bound_ws);
+  const bool out_dev = is_device_ptr(out);
+  const int64_t per = int64_t(1) << p->batch_log2;
+  double2* stage = reinterpret_cast<double2*>(ws + p->ws_out_stage);
+  // Device output: one kernel writes the chunk.  Host output: the staging area
+  // holds 2^batch_log2 complex values, so each trajectory row goes through it.
+  auto consume = [&](int phase, int64_t base, int64_t nv, int64_t tb, int64_t nt, const std::vector<int>& bpos,
+                     const std::vector<int>& tpos) -> tnq_status {
+    if (phase < 0) return TNQ_OK;
+    double2* o = reinterpret_cast<double2*>(out);
+    if (out_dev) {
+      TNQ_CUDA(launch_traj_amplitudes_out(ws + p->ws_acc, nv, 0, nt, bpos.data(), (int)bpos.size(), tpos.data(),
+                                          (int)tpos.size(), o + tb * n_bs + base, n_bs, ctx->stream));
+      ctx->launches++;
+      return TNQ_OK;
+    }
+    for (int64_t j = 0; j < nt; ++j) {
+      TNQ_CUDA(launch_traj_amplitudes_out(ws + p->ws_acc, nv, j, 1, bpos.data(), (int)bpos.size(), tpos.data(),
+                                          (int)tpos.size(), stage, per, ctx->stream));
+      ctx->launches++;
+      TNQ_CUDA(cudaMemcpyAsync(o + (tb + j) * n_bs + base, stage, 16 * size_t(nv), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+      TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return TNQ_OK;
+  };
+  auto batch_end = [&](int64_t, int64_t) -> tnq_status { return TNQ_OK; };
+  return noisy_driver(ctx, p, traj_begin, n_traj, seed, n_bs, bits, consume, batch_end);
 }
 
 // Partial-product bytes any split of an output of 2^rc elements can need.

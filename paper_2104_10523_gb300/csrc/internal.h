@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/tnq.h"
+#include "traj.cuh"
 
 namespace tnq {
 
@@ -131,6 +132,15 @@ struct Plan {
   // workspace layout (bytes)
   size_t ws_leaves = 0, ws_arena = 0, ws_arena_bytes = 0, ws_scratch_a = 0, ws_scratch_b = 0, ws_partial = 0,
          ws_scratch_bytes = 0, ws_acc = 0, ws_misc = 0, ws_total = 0;
+  // misc region: [flags 256 B][bit staging][output staging 16 B x 2^w][psum][p2sum]
+  size_t ws_bits = 0, ws_out_stage = 0, ws_psum = 0, ws_p2sum = 0;
+  // trajectory program (noisy circuits): tables uploaded at bind time
+  std::vector<TrajLeafDesc> traj_leaves;
+  std::vector<int> traj_leaf_ids;
+  std::vector<TrajFactor> traj_factors;
+  std::vector<cd> traj_mats;      // 16 entries per matrix (2x2 use stride 2)
+  std::vector<double> traj_cumq;
+  size_t ws_traj = 0, ws_traj_factors = 0, ws_traj_mats = 0, ws_traj_cumq = 0;
   int max_operand_log2 = 0;
   // device binding
   void* bound_ws = nullptr;

@@ -171,10 +171,84 @@ void layout_steps(Plan* p) {
   off = align_up(off + max_part + 256, 1024);
   p->ws_acc = off;
   off = align_up(off + 16 * (size_t(1) << p->tensors[p->root].rank), 256);
+  // trajectory program tables
+  for (size_t i = 0; i < p->traj_leaves.size(); ++i) p->traj_leaves[i].out_offset = (long long)p->tensors[p->traj_leaf_ids[i]].offset;
+  p->ws_traj = off;
+  off = align_up(off + sizeof(TrajLeafDesc) * p->traj_leaves.size(), 256);
+  p->ws_traj_factors = off;
+  off = align_up(off + sizeof(TrajFactor) * p->traj_factors.size(), 256);
+  p->ws_traj_mats = off;
+  off = align_up(off + 16 * p->traj_mats.size(), 256);
+  p->ws_traj_cumq = off;
+  off = align_up(off + 8 * p->traj_cumq.size(), 256);
   p->ws_misc = off;
-  size_t nbits = size_t(p->net.n_qubits) << p->batch_log2;
-  off = align_up(off + 256 + align_up(nbits, 256) + 16 * (size_t(1) << p->batch_log2), 256);
+  const size_t per = size_t(1) << p->batch_log2;
+  p->ws_bits = off + 256;
+  p->ws_out_stage = align_up(p->ws_bits + size_t(p->net.n_qubits) * per, 256);
+  p->ws_psum = align_up(p->ws_out_stage + 16 * per, 256);
+  p->ws_p2sum = align_up(p->ws_psum + 8 * per, 256);
+  off = align_up(p->ws_p2sum + 8 * per, 256);
   p->ws_total = off;
+}
+
+// Device program of the trajectory leaves: per leaf its factors in circuit
+// order; gate matrices as given, channels as their Kraus operators rescaled by
+// 1/sqrt(q_k) with the cumulative q table (summed in index order).
+static void build_traj_program(const Circuit& c, Plan* p) {
+  p->traj_leaves.clear();
+  p->traj_leaf_ids.clear();
+  p->traj_factors.clear();
+  p->traj_mats.clear();
+  p->traj_cumq.clear();
+  auto push_mat = [&](const std::vector<cd>& m) {
+    int idx = (int)(p->traj_mats.size() / 16);
+    std::vector<cd> e(16, cd(0, 0));
+    for (size_t i = 0; i < m.size() && i < 16; ++i) e[i] = m[i];
+    p->traj_mats.insert(p->traj_mats.end(), e.begin(), e.end());
+    return idx;
+  };
+  for (int li = 0; li < (int)p->net.leaves.size(); ++li) {
+    const Leaf& L = p->net.leaves[li];
+    if (L.kind != LEAF_TRAJ) continue;
+    TrajLeafDesc d;
+    d.n_slots = L.n_slots;
+    d.in_fixed_mask = L.in_fixed_mask;
+    d.n_factors = (int)L.factors.size();
+    d.factor_off = (int)p->traj_factors.size();
+    d.out_offset = 0;
+    d.nfree = 0;
+    for (int s = 0; s < L.n_slots; ++s) d.nfree += !((L.in_fixed_mask >> s) & 1);
+    for (const GroupFactor& g : L.factors) {
+      const COp& op = c.ops[g.op];
+      TrajFactor f;
+      f.channel = op.channel ? 1 : 0;
+      f.arity = (int)op.qubits.size();
+      f.slot_mask = g.slot_mask;
+      f.swap = g.swap ? 1 : 0;
+      f.n_ops = 0;
+      f.cum_off = 0;
+      f.chan_index = op.channel_index;
+      if (!op.channel) {
+        f.mat_off = push_mat(op.mats[0]);
+      } else {
+        f.n_ops = (int)op.mats.size();
+        f.cum_off = (int)p->traj_cumq.size();
+        double acc = 0;
+        for (int k = 0; k < f.n_ops; ++k) {
+          acc += op.kraus_q[k];
+          p->traj_cumq.push_back(acc);
+          std::vector<cd> a = op.mats[k];
+          const double s = op.kraus_q[k] > 0 ? 1.0 / std::sqrt(op.kraus_q[k]) : 0.0;
+          for (auto& z : a) z *= s;
+          int idx = push_mat(a);
+          if (k == 0) f.mat_off = idx;
+        }
+      }
+      p->traj_factors.push_back(f);
+    }
+    p->traj_leaves.push_back(d);
+    p->traj_leaf_ids.push_back(li);
+  }
 }
 
 tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) {
@@ -188,6 +262,7 @@ tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) {
   tnq_status st = build_network(c, p->batch_log2, p->traj_log2, &p->net);
   if (st != TNQ_OK) return st;
   p->hyper = make_hyper(p->net);
+  build_traj_program(c, p);
   const Hyper& h = p->hyper;
   std::vector<Tree> cands;
   int mode = o.path_mode;

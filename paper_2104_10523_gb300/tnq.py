@@ -35,7 +35,7 @@ EXPORTS = (
     "tnq_plan_bind", "tnq_amplitudes", "tnq_noisy_probabilities",
     "tnq_contract_workspace_bytes", "tnq_contract_pair",
     "tnq_ctx_launch_count", "tnq_ctx_set_timing", "tnq_ctx_get_timings",
-    "tnq_contract_pair_noalloc",
+    "tnq_contract_pair_noalloc", "tnq_trajectory_amplitudes",
 )
 
 
@@ -103,6 +103,7 @@ def load() -> C.CDLL:
         "tnq_ctx_set_timing": ([vp, i32], i32),
         "tnq_ctx_get_timings": ([vp, dp, i32, ip], i32),
         "tnq_contract_pair_noalloc": ([vp, vp, i32, ip, vp, i32, ip, vp, i32, ip], i32),
+        "tnq_trajectory_amplitudes": ([vp, vp, u64, i64, i64, i64, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -211,6 +212,12 @@ def tnq_noisy_probabilities(ctx, plan, n_traj, seed, bits, p_out, se_out=None):
                                          _ptr(p_out), _ptr(se_out)))
 
 
+def tnq_trajectory_amplitudes(ctx, plan, seed, traj_begin, n_traj, bits, out):
+    """out: float64 [n_traj][n_bs][2] (NumPy host or torch device)."""
+    check(load().tnq_trajectory_amplitudes(ctx, plan, int(seed), int(traj_begin), int(n_traj), int(bits.shape[0]),
+                                           _ptr(bits), _ptr(out)))
+
+
 def tnq_contract_workspace_bytes(precision, ra, rb, rc) -> int:
     return int(load().tnq_contract_workspace_bytes(int(precision), int(ra), int(rb), int(rc)))
 
@@ -317,6 +324,21 @@ class Context:
         out = np.empty((b.shape[0], 2), dtype=np.float64)
         tnq_amplitudes(self.h, plan.h, b, out)
         return out[:, 0] + 1j * out[:, 1]
+
+    def noisy_probabilities(self, plan: Plan, bits, n_traj, seed):
+        """(p, stderr) as float64 arrays for host int8 bits [n_bs][n]."""
+        b = np.ascontiguousarray(bits, dtype=np.int8)
+        p = np.empty(b.shape[0], dtype=np.float64)
+        se = np.empty(b.shape[0], dtype=np.float64)
+        tnq_noisy_probabilities(self.h, plan.h, n_traj, seed, b, p, se)
+        return p, se
+
+    def trajectory_amplitudes(self, plan: Plan, bits, seed, traj_begin, n_traj):
+        """complex128 [n_traj][n_bs] amplitudes of individual trajectories."""
+        b = np.ascontiguousarray(bits, dtype=np.int8)
+        out = np.empty((n_traj, b.shape[0], 2), dtype=np.float64)
+        tnq_trajectory_amplitudes(self.h, plan.h, seed, traj_begin, n_traj, b, out)
+        return out[..., 0] + 1j * out[..., 1]
 
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:
