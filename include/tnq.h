@@ -210,6 +210,14 @@ tnq_status tnq_contract_pair(tnq_ctx* ctx, const void* A, int ra, const int* a_l
 tnq_status tnq_contract_pair_noalloc(tnq_ctx* ctx, const void* A, int ra, const int* a_labels, const void* B,
                                      int rb, const int* b_labels, void* C, int rc, const int* c_labels);
 
+/* Replay full batches from a CUDA graph (1, the default) or launch every kernel
+ * directly (0).  With graphs on, the first full batch of a plan at a given
+ * precision captures every slice and step of one batch into a graph (on a
+ * private stream) and later batches replay it on the context's stream.  The
+ * results are identical either way.  Ragged last batches and timed runs
+ * (tnq_ctx_set_timing) always launch directly. */
+tnq_status tnq_ctx_set_graphs(tnq_ctx* ctx, int enable);
+
 /* ---- measurement ---------------------------------------------------------- */
 /* Number of kernels this context has launched so far (cumulative). */
 tnq_status tnq_ctx_launch_count(const tnq_ctx* ctx, uint64_t* count);

@@ -152,7 +152,11 @@ tnq_status tnq_plan_create(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_
   return TNQ_OK;
 }
 
-void tnq_plan_destroy(tnq_plan* p) { delete p; }
+void tnq_plan_destroy(tnq_plan* p) {
+  if (!p) return;
+  plan_release_graph(&p->p);
+  delete p;
+}
 
 tnq_status tnq_plan_get_info(const tnq_plan* pp, tnq_plan_info* info) {
   if (!pp || !info) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
@@ -216,6 +220,7 @@ tnq_status tnq_ctx_create(const tnq_options* o, tnq_ctx** out) {
 void tnq_ctx_destroy(tnq_ctx* c) {
   if (!c) return;
   for (auto e : c->c.ev_pool) cudaEventDestroy(e);
+  if (c->c.capture_stream) cudaStreamDestroy(c->c.capture_stream);
   delete c;
 }
 
@@ -258,6 +263,12 @@ tnq_status tnq_contract_pair(tnq_ctx* c, const void* A, int ra, const int* al, c
   if (!c || !A || !B || !C) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
   if ((ra && !al) || (rb && !bl) || (rc && !cl)) return fail(TNQ_ERR_INVALID_ARG, "NULL label array");
   return exec_contract_pair(&c->c, A, ra, al, B, rb, bl, C, rc, cl, ws, ws_bytes);
+}
+
+tnq_status tnq_ctx_set_graphs(tnq_ctx* c, int enable) {
+  if (!c) return fail(TNQ_ERR_INVALID_ARG, "NULL context");
+  c->c.use_graphs = enable != 0;
+  return TNQ_OK;
 }
 
 tnq_status tnq_ctx_launch_count(const tnq_ctx* c, uint64_t* count) {

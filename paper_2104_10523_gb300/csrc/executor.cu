@@ -7,6 +7,7 @@
 // the batch accumulator (the cross-slice sum, fixed ascending slice order).
 // The accumulator is finally mapped to bitstring order.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -275,12 +276,91 @@ tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws) {
 
 }  // namespace
 
+void plan_release_graph(Plan* p) {
+  if (p->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(p->graph_exec));
+  p->graph_exec = nullptr;
+  p->graph_precision = -1;
+}
+
+namespace {
+
+// Enqueue one full batch that reads its bitstrings from the staging buffer and
+// leaves its amplitudes (bitstring order) in the output staging buffer.
+tnq_status enqueue_batch(Ctx* ctx, Plan* p, int64_t nv, const int* pos) {
+  char* ws = static_cast<char*>(p->bound_ws);
+  const int n = p->net.n_qubits, w = p->batch_log2;
+  const int L = p->tree.n_leaves;
+  int first_proj = -1;
+  for (int i = 0; i < L; ++i)
+    if (p->net.leaves[i].kind == LEAF_PROJ) {
+      first_proj = i;
+      break;
+    }
+  size_t stride = first_proj + 1 < L ? p->tensors[first_proj + 1].offset - p->tensors[first_proj].offset : 0;
+  TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w,
+                            reinterpret_cast<const int8_t*>(ws + p->ws_bits), nv, reinterpret_cast<int*>(ws + p->ws_misc),
+                            ctx->stream));
+  ctx->launches++;
+  TNQ_CUDA(launch_zero(ws + p->ws_acc, 16 * (size_t(1) << p->tensors[p->root].rank), ctx->stream));
+  const int n_slices = 1 << p->slice_labels.size();
+  for (int s = 0; s < n_slices; ++s) {
+    tnq_status st = run_pass(ctx, p, s, ws);
+    if (st != TNQ_OK) return st;
+  }
+  TNQ_CUDA(launch_finalize(ws + p->ws_acc, ws + p->ws_out_stage, nv, pos, w, ctx->stream));
+  ctx->launches++;
+  return TNQ_OK;
+}
+
+// Capture enqueue_batch for a full batch into a graph (once per plan and precision).
+tnq_status ensure_graph(Ctx* ctx, Plan* p, const int* pos) {
+  if (p->graph_exec && p->graph_precision == ctx->precision) return TNQ_OK;
+  plan_release_graph(p);
+  auto t0 = std::chrono::steady_clock::now();
+  if (ctx->precision != TNQ_PREC_FP32) TNQ_CUDA(tc_gemm_prepare());
+  // capture on a private stream (the legacy default stream cannot be captured);
+  // the graph is launched on the context's stream
+  if (!ctx->capture_stream) TNQ_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  const uint64_t launches_before = ctx->launches;
+  cudaStream_t user_stream = ctx->stream;
+  ctx->stream = ctx->capture_stream;
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    ctx->stream = user_stream;
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  tnq_status st = enqueue_batch(ctx, p, int64_t(1) << p->batch_log2, pos);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(ctx->stream, &g);
+  ctx->stream = user_stream;
+  ctx->launches = launches_before;  // captured, not launched
+  if (st != TNQ_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  size_t nodes = 0;
+  cudaGraphGetNodes(g, nullptr, &nodes);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  p->graph_exec = ex;
+  p->graph_precision = ctx->precision;
+  p->graph_nodes = (int64_t)nodes;
+  p->graph_capture_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return TNQ_OK;
+}
+
+}  // namespace
+
 tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes) {
   if (!ws) return fail(TNQ_ERR_WORKSPACE, "workspace is NULL");
   if (bytes < p->ws_total)
     return fail(TNQ_ERR_WORKSPACE, "workspace too small: need " + std::to_string(p->ws_total) + " bytes");
   if (!is_device_ptr(ws)) return fail(TNQ_ERR_WORKSPACE, "workspace must be device memory");
   TNQ_CUDA(cudaSetDevice(ctx->device));
+  plan_release_graph(p);
   char* base = static_cast<char*>(ws);
   std::vector<float> buf;
   for (size_t i = 0; i < p->net.leaves.size(); ++i) {
@@ -348,8 +428,21 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
   TNQ_CUDA(cudaMemsetAsync(err_flag, 0, 2 * sizeof(int), ctx->stream));
   const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
   const int n_slices = 1 << p->slice_labels.size();
+  const bool graphs = ctx->use_graphs && !ctx->timing;
   for (int64_t base = 0; base < n_bs; base += per) {
     int64_t nv = std::min<int64_t>(per, n_bs - base);
+    if (graphs && nv == per) {
+      // full batch: stage the bitstrings, replay the captured graph, copy out
+      TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * n, size_t(nv) * n,
+                               bits_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+      tnq_status st = ensure_graph(ctx, p, pos.data());
+      if (st != TNQ_OK) return st;
+      TNQ_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(p->graph_exec), ctx->stream));
+      ctx->launches += uint64_t(p->graph_nodes);
+      TNQ_CUDA(cudaMemcpyAsync(out + 2 * base, out_stage, size_t(nv) * 16,
+                               out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+      continue;
+    }
     const int8_t* bsrc;
     if (bits_dev) {
       bsrc = bits + base * n;

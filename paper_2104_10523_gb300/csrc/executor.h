@@ -30,7 +30,11 @@ struct Ctx {
   std::vector<std::pair<int, KernelRecord>> pending;  // (event index, record)
   std::vector<KernelRecord> records;
   int cur_step = -1;
+  bool use_graphs = true;        // replay full batches from a captured CUDA graph
+  cudaStream_t capture_stream = nullptr;  // private stream graphs are captured on
 };
+
+void plan_release_graph(Plan* p);
 
 // Timing helpers: bracket a launch when ctx->timing is set.
 int timing_begin(Ctx* ctx);

@@ -45,6 +45,7 @@ constexpr int TC_ROW_BYTES = 128;     // one 128B swizzle atom of K per stage
 constexpr int TC_MAX_STAGES = 8;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 constexpr int TC_SMEM_BUDGET = 200 * 1024;
+constexpr int TC_GROUP_M = 16;         // m-tiles per launch-order group
 
 struct TcParams {
   int M;          // complex rows per batch (A' has 2M rows)
@@ -159,13 +160,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Launch order: within each (split, batch) the output tiles go in groups of
+  // TC_GROUP_M m-tiles with the n-tiles swept inside a group, so the CTAs of one
+  // wave share a few A' tile rows and B tiles in L2.
   long long bid = blockIdx.x;
-  const int mt = int(bid % P.tiles_m);
-  bid /= P.tiles_m;
-  const int nt = int(bid % P.tiles_n);
-  bid /= P.tiles_n;
+  const long long tiles = (long long)P.tiles_m * P.tiles_n;
+  const int pid = int(bid % tiles);
+  bid /= tiles;
   const int split = int(bid % P.splits);
   const int h = int(bid / P.splits);
+  const int per_group = TC_GROUP_M * P.tiles_n;
+  const int first_m = (pid / per_group) * TC_GROUP_M;
+  const int group_m = min(P.tiles_m - first_m, TC_GROUP_M);
+  const int mt = first_m + (pid % per_group) % group_m;
+  const int nt = (pid % per_group) / group_m;
   const int kb_begin = split * P.kb_per_split;
   const int nkb = min(P.nkb - kb_begin, P.kb_per_split);  // K blocks of this CTA (>= 1)
   const uint32_t stage_bytes = (P.split ? 2u : 1u) * (P.a_bytes + P.b_bytes);
@@ -406,6 +414,19 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t inner, uint6
 
 }  // namespace
 
+cudaError_t tc_gemm_prepare() {
+  // one-time set-up outside any stream capture: the driver entry point and the
+  // largest dynamic shared memory any configuration of the kernel uses
+  static cudaError_t result = cudaErrorUnknown;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    result = encode_fn() ? cudaSuccess : cudaErrorNotSupported;
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BUDGET + 1024);
+  });
+  return result;
+}
+
 bool tc_gemm_supported(int M, int N, int K, int precision) {
   if (precision == TNQ_PREC_FP32) return false;
   const bool bf16 = precision == TNQ_PREC_BF16X3;
@@ -465,12 +486,8 @@ cudaError_t launch_cgemm_tc(const TcGemmArgs& g, int sm_count, cudaStream_t st) 
     mb_lo = mb_hi;
   }
   const int smem = int(P.stages * stage_bytes) + 1024;
-  static int configured = 0;
-  if (configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t pe = tc_gemm_prepare();
+  if (pe != cudaSuccess) return pe;
   cgemm_tc_kernel<<<unsigned(total), TC_THREADS, smem, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, P);
   if (g.splits_used) *g.splits_used = P.splits;
   return cudaGetLastError();

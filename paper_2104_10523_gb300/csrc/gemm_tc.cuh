@@ -23,6 +23,9 @@ struct TcGemmArgs {
   int* splits_used = nullptr;  // out: splits actually launched
 };
 
+// One-time set-up (driver entry point, shared-memory limit); call outside capture.
+cudaError_t tc_gemm_prepare();
+
 // Whether a GEMM of this shape and precision runs on the tensor cores.
 bool tc_gemm_supported(int M, int N, int K, int precision);
 

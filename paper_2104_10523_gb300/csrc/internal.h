@@ -142,6 +142,11 @@ struct Plan {
   std::vector<double> traj_cumq;
   size_t ws_traj = 0, ws_traj_factors = 0, ws_traj_mats = 0, ws_traj_cumq = 0;
   int max_operand_log2 = 0;
+  // CUDA graph of one full batch (every slice and step), per precision
+  void* graph_exec = nullptr;     // cudaGraphExec_t
+  int graph_precision = -1;
+  double graph_capture_ms = 0;
+  int64_t graph_nodes = 0;
   // device binding
   void* bound_ws = nullptr;
   size_t bound_bytes = 0;

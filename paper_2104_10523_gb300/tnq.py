@@ -35,7 +35,7 @@ EXPORTS = (
     "tnq_plan_bind", "tnq_amplitudes", "tnq_noisy_probabilities",
     "tnq_contract_workspace_bytes", "tnq_contract_pair",
     "tnq_ctx_launch_count", "tnq_ctx_set_timing", "tnq_ctx_get_timings",
-    "tnq_contract_pair_noalloc", "tnq_trajectory_amplitudes",
+    "tnq_contract_pair_noalloc", "tnq_trajectory_amplitudes", "tnq_ctx_set_graphs",
 )
 
 
@@ -104,6 +104,7 @@ def load() -> C.CDLL:
         "tnq_ctx_get_timings": ([vp, dp, i32, ip], i32),
         "tnq_contract_pair_noalloc": ([vp, vp, i32, ip, vp, i32, ip, vp, i32, ip], i32),
         "tnq_trajectory_amplitudes": ([vp, vp, u64, i64, i64, i64, vp, vp], i32),
+        "tnq_ctx_set_graphs": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -233,6 +234,10 @@ def tnq_contract_pair_noalloc(ctx, A, a_labels, B, b_labels, Cout, c_labels):
     check(load().tnq_contract_pair_noalloc(ctx, _ptr(A), len(a_labels), _int_array(a_labels), _ptr(B),
                                            len(b_labels), _int_array(b_labels), _ptr(Cout), len(c_labels),
                                            _int_array(c_labels)))
+
+
+def tnq_ctx_set_graphs(ctx, enable: bool):
+    check(load().tnq_ctx_set_graphs(ctx, 1 if enable else 0))
 
 
 def tnq_ctx_launch_count(ctx) -> int:

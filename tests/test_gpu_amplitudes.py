@@ -96,6 +96,23 @@ def test_ragged_batch_and_device_buffers(T, small_ref):
     assert ctx.amplitudes(plan, CONFIG_SMALL_BITS[:0]).shape == (0,)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_graph_replay_identical_to_direct_launches(T, prec):
+    c = grid_circuit(4, 4, 8, 3)
+    bits = random_bitstrings(16, 40, 8)   # 2 full batches of 16 and a ragged one
+    ctx = T.Context(0, prec)
+    plan = T.Plan(T.Circuit(c), batch_log2=4, max_intermediate_log2=9, path_mode=0)
+    ctx.bind(plan)
+    assert plan.info["n_sliced"] >= 1
+    T.tnq_ctx_set_graphs(ctx.h, False)
+    direct = ctx.amplitudes(plan, bits)
+    T.tnq_ctx_set_graphs(ctx.h, True)
+    g1 = ctx.amplitudes(plan, bits)
+    g2 = ctx.amplitudes(plan, bits)   # replay of the captured graph
+    assert np.array_equal(direct, g1) and np.array_equal(g1, g2)
+    assert rel_l2(g1, sv.amplitudes(c, bits)) <= TOL[prec]
+
+
 def test_bad_bits_rejected(T, small_ref):
     c, _ = small_ref
     ctx = T.Context(0, "fp32")
