@@ -334,3 +334,60 @@ def test_trajectory_mean_within_stderr_of_density_matrix():
     mean, se = noise.noisy_probabilities(c, bits, 3000, seed=11,
                                          amplitude_fn=lambda cc, b, p: sv.amplitudes(cc, b, p))
     assert np.all(np.abs(mean - exact) <= 4 * se + 1e-12)
+
+
+# ---------------------------------------------------------------- cost-model MLP
+def test_mlp_gradients_match_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    P = mlp.init_params(5, 7, seed=1)
+    for k in ("b1", "b2", "b3"):
+        P[k] = rng.standard_normal(P[k].shape) * 0.1   # non-zero biases exercise every path
+    X = rng.standard_normal((9, 5))
+    t = rng.standard_normal(9)
+    G = mlp.gradients(P, X, t)
+    h = 1e-6
+    for k in mlp.PARAMS:
+        num = np.zeros_like(P[k])
+        for idx in np.ndindex(P[k].shape):
+            Pp = {q: v.copy() for q, v in P.items()}
+            Pm = {q: v.copy() for q, v in P.items()}
+            Pp[k][idx] += h
+            Pm[k][idx] -= h
+            num[idx] = (mlp.loss(Pp, X, t) - mlp.loss(Pm, X, t)) / (2 * h)
+        assert np.allclose(G[k], num, rtol=1e-5, atol=1e-8), k
+
+
+def test_mlp_linear_regime_is_least_squares_gradient():
+    """With every hidden unit active and W2 = I, the model is linear in x and the
+    gradient of the last layer equals the textbook least-squares gradient."""
+    from oracle import mlp
+    rng = np.random.default_rng(2)
+    d, h, B = 3, 4, 6
+    P = {"W1": np.abs(rng.standard_normal((d, h))), "b1": np.full(h, 10.0),
+         "W2": np.eye(h), "b2": np.zeros(h), "W3": rng.standard_normal((h, 1)), "b3": np.zeros(1)}
+    X = np.abs(rng.standard_normal((B, d)))
+    t = rng.standard_normal(B)
+    A = X @ P["W1"] + P["b1"]                       # all positive, so relu is the identity
+    y = A @ P["W3"][:, 0]
+    g_ls = 2.0 / B * A.T @ (y - t)
+    assert np.allclose(mlp.gradients(P, X, t)["W3"][:, 0], g_ls, atol=1e-12)
+
+
+def test_adam_first_step_moves_by_lr_sign():
+    """Adam's first bias-corrected step is lr * g / (|g| + eps): magnitude lr."""
+    from oracle import mlp
+    P = {k: np.zeros((2, 2)) for k in mlp.PARAMS}
+    G = {k: np.array([[1.0, -2.0], [0.5, 0.0]]) for k in mlp.PARAMS}
+    st = {}
+    mlp.adam_step(P, G, st, lr=0.01, step=1)
+    want = -0.01 * np.array([[1.0, -1.0], [1.0, 0.0]])
+    assert np.allclose(P["W1"], want, atol=1e-9)
+
+
+def test_bf16_rounding_known_values():
+    from oracle import mlp
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: ties go to even (1.0);
+    # 1 + 3*2^-9 rounds up to 1 + 2^-7; powers of two are exact.
+    x = np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 0.75, -3.0, 2.0 ** -20])
+    assert np.array_equal(mlp.bf16_round(x), [1.0, 1.0 + 2 ** -7, 0.75, -3.0, 2.0 ** -20])
