@@ -218,6 +218,53 @@ tnq_status tnq_contract_pair_noalloc(tnq_ctx* ctx, const void* A, int ra, const 
  * (tnq_ctx_set_timing) always launch directly. */
 tnq_status tnq_ctx_set_graphs(tnq_ctx* ctx, int enable);
 
+/* ---- learned path cost model ----------------------------------------------- */
+/* A 3-layer MLP (d_in -> hidden -> hidden -> 1, ReLU; BF16 weights with FP32
+ * master copies and FP32 accumulation) that predicts ln(microseconds) of one
+ * contraction step from its features, trained by Adam on MSE with the
+ * library's own GPU kernels on step timings the contractor records
+ * (tnq_ctx_get_timings).  A plan's predicted time is the sum of its steps'
+ * exp(prediction) times its slice count.  The paper motivates ranking paths
+ * by measured cost rather than FLOPs (Sec. 4.3: a path with more flops ran
+ * more efficiently) but gives no model.
+ * Parameters are one flat FP32 vector: W1 [d_in][hidden], b1 [hidden],
+ * W2 [hidden][hidden], b2 [hidden], W3 [hidden][1], b3 [1]. */
+typedef struct tnq_cost_model tnq_cost_model;
+int tnq_step_feature_count(void);
+/* d_in must equal tnq_step_feature_count(); weights He-uniform from `seed`. */
+tnq_status tnq_cost_model_create(int d_in, int hidden, int max_batch, uint64_t seed, tnq_cost_model** out);
+void tnq_cost_model_destroy(tnq_cost_model* m);
+size_t tnq_cost_model_workspace_bytes(const tnq_cost_model* m);
+int64_t tnq_cost_model_n_params(const tnq_cost_model* m);
+/* Bind a caller-owned device workspace (weights, Adam state, activations). */
+tnq_status tnq_cost_model_bind(tnq_ctx* ctx, tnq_cost_model* m, void* workspace, size_t bytes);
+/* Host FP32 parameter vector in / out (set resets the Adam state). */
+tnq_status tnq_cost_model_set_params(tnq_ctx* ctx, tnq_cost_model* m, const float* params);
+tnq_status tnq_cost_model_get_params(tnq_ctx* ctx, tnq_cost_model* m, float* params);
+/* One forward and backward pass on n <= max_batch host rows X [n][d_in] with
+ * targets t [n]: gradients of the mean squared error (host, parameter layout)
+ * and the loss.  grads or loss may be NULL. */
+tnq_status tnq_cost_model_gradients(tnq_ctx* ctx, tnq_cost_model* m, const float* X, const float* t, int64_t n,
+                                    float* grads, float* loss);
+/* Adam training on host rows (seeded minibatch order per epoch). */
+tnq_status tnq_cost_model_train(tnq_ctx* ctx, tnq_cost_model* m, const float* X, const float* t, int64_t n,
+                                int epochs, int batch, float lr, float* final_loss);
+/* Predictions y [n] for host rows X [n][d_in]. */
+tnq_status tnq_cost_model_predict(tnq_ctx* ctx, tnq_cost_model* m, const float* X, int64_t n, float* y);
+/* Features of every step of a plan for the kernels `precision` runs them on:
+ * out [n_steps][tnq_step_feature_count()]. */
+tnq_status tnq_plan_step_features(const tnq_plan* p, int precision, float* out);
+/* As tnq_plan_create (BEST candidate set), but the candidate with the least
+ * predicted time (at the context's precision) wins instead of the one with
+ * the fewest flops. */
+tnq_status tnq_plan_create_learned(tnq_ctx* ctx, tnq_cost_model* m, const tnq_circuit* c,
+                                   const tnq_plan_opts* opts, tnq_plan** out);
+/* Candidates the search examined: sliced flops per batch (-1 if infeasible)
+ * and predicted milliseconds (-1 unless learned), the flop-minimal index and
+ * the chosen index.  Copies min(max, *n) entries. */
+tnq_status tnq_plan_get_candidates(const tnq_plan* p, double* flops, double* predicted_ms, int max, int* n,
+                                   int* flopmin, int* chosen);
+
 /* ---- measurement ---------------------------------------------------------- */
 /* Number of kernels this context has launched so far (cumulative). */
 tnq_status tnq_ctx_launch_count(const tnq_ctx* ctx, uint64_t* count);

@@ -7,6 +7,7 @@
 
 #include "executor.h"
 #include "internal.h"
+#include "mlp.h"
 
 namespace tnq {
 
@@ -263,6 +264,119 @@ tnq_status tnq_contract_pair(tnq_ctx* c, const void* A, int ra, const int* al, c
   if (!c || !A || !B || !C) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
   if ((ra && !al) || (rb && !bl) || (rc && !cl)) return fail(TNQ_ERR_INVALID_ARG, "NULL label array");
   return exec_contract_pair(&c->c, A, ra, al, B, rb, bl, C, rc, cl, ws, ws_bytes);
+}
+
+// ---- learned path cost model
+tnq_status tnq_cost_model_create(int d_in, int hidden, int max_batch, uint64_t seed, tnq_cost_model** out) {
+  if (!out) return fail(TNQ_ERR_INVALID_ARG, "out is NULL");
+  if (d_in != kStepFeatures) return fail(TNQ_ERR_INVALID_ARG, "d_in must equal tnq_step_feature_count()");
+  if (hidden < 1 || hidden > 4096 || max_batch < 1 || max_batch > (1 << 20))
+    return fail(TNQ_ERR_INVALID_ARG, "hidden must be in [1, 4096] and max_batch in [1, 2^20]");
+  auto* m = new (std::nothrow) tnq_cost_model();
+  if (!m) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  m->m.d_in = d_in;
+  m->m.h = hidden;
+  m->m.max_batch = max_batch;
+  m->m.seed = seed;
+  m->m.layout();
+  mlp_init(&m->m);
+  *out = m;
+  return TNQ_OK;
+}
+
+void tnq_cost_model_destroy(tnq_cost_model* m) { delete m; }
+
+size_t tnq_cost_model_workspace_bytes(const tnq_cost_model* m) { return m ? m->m.ws_bytes : 0; }
+
+int64_t tnq_cost_model_n_params(const tnq_cost_model* m) { return m ? (int64_t)m->m.n_params() : 0; }
+
+int tnq_step_feature_count(void) { return kStepFeatures; }
+
+tnq_status tnq_cost_model_bind(tnq_ctx* c, tnq_cost_model* m, void* ws, size_t bytes) {
+  if (!c || !m) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return mlp_bind(&c->c, &m->m, ws, bytes);
+}
+
+tnq_status tnq_cost_model_set_params(tnq_ctx* c, tnq_cost_model* m, const float* params) {
+  if (!c || !m || !params) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return mlp_upload(&c->c, &m->m, params);
+}
+
+tnq_status tnq_cost_model_get_params(tnq_ctx* c, tnq_cost_model* m, float* params) {
+  if (!c || !m || !params) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return mlp_download(&c->c, &m->m, params);
+}
+
+tnq_status tnq_cost_model_gradients(tnq_ctx* c, tnq_cost_model* m, const float* X, const float* t, int64_t n,
+                                    float* grads, float* loss) {
+  if (!c || !m || !X || !t) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return mlp_gradients(&c->c, &m->m, X, t, n, grads, loss);
+}
+
+tnq_status tnq_cost_model_train(tnq_ctx* c, tnq_cost_model* m, const float* X, const float* t, int64_t n, int epochs,
+                                int batch, float lr, float* final_loss) {
+  if (!c || !m || !X || !t) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return mlp_train(&c->c, &m->m, X, t, n, epochs, batch, lr, final_loss);
+}
+
+tnq_status tnq_cost_model_predict(tnq_ctx* c, tnq_cost_model* m, const float* X, int64_t n, float* y) {
+  if (!c || !m || !X || !y) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (n < 0) return fail(TNQ_ERR_INVALID_ARG, "n must be >= 0");
+  return mlp_predict(&c->c, &m->m, X, n, y);
+}
+
+tnq_status tnq_plan_step_features(const tnq_plan* p, int precision, float* out) {
+  if (!p || !out) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  std::vector<float> f;
+  step_features(p->p, precision, &f);
+  std::copy(f.begin(), f.end(), out);
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_create_learned(tnq_ctx* c, tnq_cost_model* m, const tnq_circuit* circ, const tnq_plan_opts* o,
+                                   tnq_plan** out) {
+  if (!c || !m || !circ || !o || !out) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (!m->m.ws) return fail(TNQ_ERR_WORKSPACE, "cost model has no bound workspace");
+  auto* p = new (std::nothrow) tnq_plan();
+  if (!p) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  Ctx* ctx = &c->c;
+  CostModel* cm = &m->m;
+  // predicted pass time = sum over steps of exp(model(features)) (the model predicts ln microseconds)
+  CandidateRanker rank = [ctx, cm](const Plan& cand, double* t) -> tnq_status {
+    std::vector<float> f;
+    step_features(cand, ctx->precision, &f);
+    const int64_t n = int64_t(f.size()) / kStepFeatures;
+    std::vector<float> y(n);
+    tnq_status s = mlp_predict(ctx, cm, f.data(), n, y.data());
+    if (s != TNQ_OK) return s;
+    double sum = 0;
+    for (float v : y) sum += std::exp(double(v));
+    *t = sum * 1e-3;  // milliseconds
+    return TNQ_OK;
+  };
+  tnq_plan_opts o2 = *o;
+  if (o2.path_mode == TNQ_PATH_GREEDY) o2.path_mode = TNQ_PATH_BEST;
+  tnq_status s = make_plan_ranked(circ->c, o2, &p->p, &rank);
+  if (s != TNQ_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_get_candidates(const tnq_plan* pp, double* flops, double* predicted_ms, int max, int* n,
+                                   int* flopmin, int* chosen) {
+  if (!pp || !n) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  const Plan& p = pp->p;
+  *n = (int)p.cand_flops.size();
+  for (int i = 0; i < max && i < *n; ++i) {
+    if (flops) flops[i] = p.cand_flops[i];
+    if (predicted_ms) predicted_ms[i] = p.cand_pred[i];
+  }
+  if (flopmin) *flopmin = p.cand_flopmin;
+  if (chosen) *chosen = p.cand_chosen;
+  return TNQ_OK;
 }
 
 tnq_status tnq_ctx_set_graphs(tnq_ctx* c, int enable) {

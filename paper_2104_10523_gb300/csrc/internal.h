@@ -9,6 +9,7 @@
 #pragma once
 
 #include <complex>
+#include <functional>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -142,6 +143,10 @@ struct Plan {
   std::vector<double> traj_cumq;
   size_t ws_traj = 0, ws_traj_factors = 0, ws_traj_mats = 0, ws_traj_cumq = 0;
   int max_operand_log2 = 0;
+  // candidate trees examined by the search: sliced flops per batch, predicted
+  // time (learned ranking, else -1), the flop-minimal one and the chosen one
+  std::vector<double> cand_flops, cand_pred;
+  int cand_flopmin = -1, cand_chosen = -1;
   // CUDA graph of one full batch (every slice and step), per precision
   void* graph_exec = nullptr;     // cudaGraphExec_t
   int graph_precision = -1;
@@ -154,6 +159,9 @@ struct Plan {
 };
 
 tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p);
+// A ranker returns the predicted time of one pass of a laid-out candidate plan.
+using CandidateRanker = std::function<tnq_status(const Plan&, double*)>;
+tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, const CandidateRanker* ranker);
 void layout_steps(Plan* p);
 
 }  // namespace tnq

@@ -19,6 +19,8 @@
 
 #include "internal.h"
 #include "splitk.h"
+#include "gemm_tc.cuh"
+#include "mlp.h"
 
 namespace tnq {
 
@@ -251,7 +253,46 @@ static void build_traj_program(const Circuit& c, Plan* p) {
   }
 }
 
-tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) {
+// Per-step features for the cost model (16 floats per step): log2 sizes of the
+// batch, row, column and contracted dimensions and of the work, operand and
+// output elements (scaled by 1/32), whether each operand is permuted, which
+// kernel the executor dispatches the step to at this precision, log2 of the
+// algorithmic bytes, and whether it is the root step.
+void step_features(const Plan& p, int precision, std::vector<float>* out) {
+  out->clear();
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    const Step& s = p.steps[i];
+    const int work = s.nH + s.nM + s.nN + s.nK;
+    const bool tc = precision != TNQ_PREC_FP32 && !skinny(s.nM, s.nN) &&
+                    tc_gemm_supported(1 << s.nM, 1 << s.nN, 1 << s.nK, precision) && work >= 18;
+    const bool dot = !tc && use_dot(s.nM, s.nN, s.nK);
+    const bool rows = !tc && !dot && skinny(s.nM, s.nN);
+    const bool simt = !tc && !dot && !rows;
+    const double bytes = 8.0 * (std::ldexp(1.0, (int)s.a_req.size()) + std::ldexp(1.0, (int)s.b_req.size()) +
+                                std::ldexp(1.0, (int)s.out_labels.size()));
+    const float f[kStepFeatures] = {s.nH / 32.f,
+                                    s.nM / 32.f,
+                                    s.nN / 32.f,
+                                    s.nK / 32.f,
+                                    work / 32.f,
+                                    float(s.a_req.size()) / 32.f,
+                                    float(s.b_req.size()) / 32.f,
+                                    float(s.out_labels.size()) / 32.f,
+                                    s.perm_a ? 1.f : 0.f,
+                                    s.perm_b ? 1.f : 0.f,
+                                    tc ? 1.f : 0.f,
+                                    rows ? 1.f : 0.f,
+                                    dot ? 1.f : 0.f,
+                                    simt ? 1.f : 0.f,
+                                    float(std::log2(bytes)) / 32.f,
+                                    i + 1 == p.steps.size() ? 1.f : 0.f};
+    out->insert(out->end(), f, f + kStepFeatures);
+  }
+}
+
+tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) { return make_plan_ranked(c, o, p, nullptr); }
+
+tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, const CandidateRanker* ranker) {
   auto t0 = std::chrono::steady_clock::now();
   if (o.batch_log2 < 0 || o.batch_log2 > 16 || o.traj_log2 < 0 || o.traj_log2 > 16)
     return fail(TNQ_ERR_INVALID_ARG, "batch_log2/traj_log2 must be in [0, 16]");
@@ -335,6 +376,39 @@ tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) {
       best_slices = slices[i];
     }
   }
+  // record every candidate's sliced flops; a ranker may override the choice
+  p->cand_flops = totals;
+  p->cand_pred.assign(NC, -1.0);
+  p->cand_flopmin = best;
+  if (best >= 0 && ranker) {
+    int pick = -1;
+    double pick_t = 0;
+    for (int i = 0; i < NC; ++i) {
+      if (totals[i] < 0) continue;
+      Plan tmp;
+      tmp.net = p->net;
+      tmp.hyper = p->hyper;
+      tmp.tree = cands[i];
+      tmp.batch_log2 = p->batch_log2;
+      tmp.traj_log2 = p->traj_log2;
+      tmp.sliced.assign(h.n_labels, 0);
+      tmp.slice_labels = slices[i];
+      for (int l : slices[i]) tmp.sliced[l] = 1;
+      layout_steps(&tmp);
+      double t = 0;
+      tnq_status rs = (*ranker)(tmp, &t);
+      if (rs != TNQ_OK) return rs;
+      t *= std::ldexp(1.0, (int)slices[i].size());
+      p->cand_pred[i] = t;
+      if (pick < 0 || t < pick_t) {
+        pick = i;
+        pick_t = t;
+      }
+    }
+    best = pick;
+    best_slices = slices[best];
+  }
+  p->cand_chosen = best;
   if (best < 0)
     return fail(TNQ_ERR_PLAN_INFEASIBLE,
                 "no contraction tree and slicing keeps every intermediate within 2^" +

@@ -36,6 +36,10 @@ EXPORTS = (
     "tnq_contract_workspace_bytes", "tnq_contract_pair",
     "tnq_ctx_launch_count", "tnq_ctx_set_timing", "tnq_ctx_get_timings",
     "tnq_contract_pair_noalloc", "tnq_trajectory_amplitudes", "tnq_ctx_set_graphs",
+    "tnq_step_feature_count", "tnq_cost_model_create", "tnq_cost_model_destroy", "tnq_cost_model_workspace_bytes",
+    "tnq_cost_model_n_params", "tnq_cost_model_bind", "tnq_cost_model_set_params", "tnq_cost_model_get_params",
+    "tnq_cost_model_gradients", "tnq_cost_model_train", "tnq_cost_model_predict", "tnq_plan_step_features",
+    "tnq_plan_create_learned", "tnq_plan_get_candidates",
 )
 
 
@@ -78,6 +82,7 @@ def load() -> C.CDLL:
     L = C.CDLL(path)
     vp, ip, i32, i64, u64, dp, sz = C.c_void_p, C.POINTER(C.c_int), C.c_int, C.c_int64, C.c_uint64, \
         C.POINTER(C.c_double), C.c_size_t
+    fp = C.POINTER(C.c_float)
     sig = {
         "tnq_version": ([], C.c_char_p),
         "tnq_status_string": ([i32], C.c_char_p),
@@ -105,6 +110,20 @@ def load() -> C.CDLL:
         "tnq_contract_pair_noalloc": ([vp, vp, i32, ip, vp, i32, ip, vp, i32, ip], i32),
         "tnq_trajectory_amplitudes": ([vp, vp, u64, i64, i64, i64, vp, vp], i32),
         "tnq_ctx_set_graphs": ([vp, i32], i32),
+        "tnq_step_feature_count": ([], i32),
+        "tnq_cost_model_create": ([i32, i32, i32, u64, C.POINTER(vp)], i32),
+        "tnq_cost_model_destroy": ([vp], None),
+        "tnq_cost_model_workspace_bytes": ([vp], sz),
+        "tnq_cost_model_n_params": ([vp], i64),
+        "tnq_cost_model_bind": ([vp, vp, vp, sz], i32),
+        "tnq_cost_model_set_params": ([vp, vp, fp], i32),
+        "tnq_cost_model_get_params": ([vp, vp, fp], i32),
+        "tnq_cost_model_gradients": ([vp, vp, fp, fp, i64, fp, fp], i32),
+        "tnq_cost_model_train": ([vp, vp, fp, fp, i64, i32, i32, C.c_float, fp], i32),
+        "tnq_cost_model_predict": ([vp, vp, fp, i64, fp], i32),
+        "tnq_plan_step_features": ([vp, i32, fp], i32),
+        "tnq_plan_create_learned": ([vp, vp, vp, C.POINTER(TnqPlanOpts), C.POINTER(vp)], i32),
+        "tnq_plan_get_candidates": ([vp, dp, dp, i32, ip, ip, ip], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -262,6 +281,89 @@ def tnq_ctx_get_timings(ctx) -> np.ndarray:
     return rec[:n.value]
 
 
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def tnq_plan_step_features(plan_h, precision, n_steps) -> np.ndarray:
+    d = load().tnq_step_feature_count()
+    out = np.zeros((n_steps, d), dtype=np.float32)
+    check(load().tnq_plan_step_features(plan_h, int(precision), _fptr(out)))
+    return out
+
+
+def tnq_plan_get_candidates(plan_h) -> dict:
+    n, fm, ch = C.c_int(), C.c_int(), C.c_int()
+    check(load().tnq_plan_get_candidates(plan_h, None, None, 0, C.byref(n), C.byref(fm), C.byref(ch)))
+    fl = np.zeros(max(n.value, 1))
+    pr = np.zeros(max(n.value, 1))
+    check(load().tnq_plan_get_candidates(plan_h, fl.ctypes.data_as(C.POINTER(C.c_double)),
+                                         pr.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n),
+                                         C.byref(fm), C.byref(ch)))
+    return {"flops": fl[:n.value], "predicted_ms": pr[:n.value], "flopmin": fm.value, "chosen": ch.value}
+
+
+class CostModel:
+    """Owns a tnq_cost_model and its device workspace (a torch tensor)."""
+
+    def __init__(self, ctx, hidden=256, max_batch=4096, seed=0):
+        import torch
+        L = load()
+        self.ctx = ctx
+        self.d_in = L.tnq_step_feature_count()
+        self.h = C.c_void_p()
+        check(L.tnq_cost_model_create(self.d_in, hidden, max_batch, seed, C.byref(self.h)))
+        nb = int(L.tnq_cost_model_workspace_bytes(self.h))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=f"cuda:{ctx.device}")
+        check(L.tnq_cost_model_bind(ctx.h, self.h, C.c_void_p(self.ws.data_ptr()), nb))
+        self.n_params = int(L.tnq_cost_model_n_params(self.h))
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        check(load().tnq_cost_model_set_params(self.ctx.h, self.h, _fptr(p)))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        check(load().tnq_cost_model_get_params(self.ctx.h, self.h, _fptr(p)))
+        return p
+
+    def gradients(self, X, t):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        check(load().tnq_cost_model_gradients(self.ctx.h, self.h, _fptr(X), _fptr(t), X.shape[0], _fptr(g),
+                                              _fptr(loss)))
+        return g, float(loss[0])
+
+    def train(self, X, t, epochs=20, batch=1024, lr=1e-3):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        check(load().tnq_cost_model_train(self.ctx.h, self.h, _fptr(X), _fptr(t), X.shape[0], epochs, batch,
+                                          C.c_float(lr), _fptr(loss)))
+        return float(loss[0])
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(X.shape[0], dtype=np.float32)
+        check(load().tnq_cost_model_predict(self.ctx.h, self.h, _fptr(X), X.shape[0], _fptr(y)))
+        return y
+
+    def plan(self, circuit, **opts):
+        """A Plan whose candidate tree is chosen by predicted time."""
+        o = TnqPlanOpts(opts.get("max_intermediate_log2", 28), opts.get("batch_log2", 0), opts.get("traj_log2", 0),
+                        opts.get("path_mode", TNQ_PATH_BEST), opts.get("n_candidates", 16), opts.get("seed", 0))
+        h = C.c_void_p()
+        check(load().tnq_plan_create_learned(self.ctx.h, self.h, circuit.h, C.byref(o), C.byref(h)))
+        return Plan.from_handle(circuit, h)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.tnq_cost_model_destroy(self.h)
+            self.h = None
+
+
 # ---------------------------------------------------------------- owning helpers
 class Circuit:
     """Owns a tnq_circuit built from a workloads.Circuit (gates and channels in order)."""
@@ -290,8 +392,24 @@ class Plan:
         self.info = tnq_plan_get_info(self.h)
         self.workspace = None
 
+    @classmethod
+    def from_handle(cls, circuit, h):
+        self = cls.__new__(cls)
+        self.circuit = circuit
+        self.h = h
+        self.info = tnq_plan_get_info(h)
+        self.workspace = None
+        return self
+
     def steps(self):
         return tnq_plan_get_steps(self.h, self.info["n_steps"])
+
+    def features(self, precision):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        return tnq_plan_step_features(self.h, prec, self.info["n_steps"])
+
+    def candidates(self):
+        return tnq_plan_get_candidates(self.h)
 
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:

@@ -211,3 +211,14 @@ CONFIG_LARGE = dict(rows=6, cols=6, cycles=14, seed=2104, n_bitstrings=1024, bit
                     max_intermediate_log2=28)
 CONFIG_NOISY = dict(rows=4, cols=5, cycles=10, seed=2021, p_depol=1e-3, gamma=1e-3,
                     n_trajectories=4096, traj_seed=7, n_bitstrings=256, bits_seed=77)
+
+
+def cost_model_circuit(seed: int) -> Circuit:
+    """Circuit `seed` of the path-cost-model workload: grid rows uniform in
+    {4,5,6}, columns in {4..7}, cycles in {8..16} (drawn from `seed`), then the
+    grid random circuit of that shape with the same seed."""
+    rng = np.random.default_rng(1_000_003 + seed)
+    rows = int(rng.integers(4, 7))
+    cols = int(rng.integers(4, 8))
+    cycles = int(rng.integers(8, 17))
+    return grid_circuit(rows, cols, cycles, seed)
