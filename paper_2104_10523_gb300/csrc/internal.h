@@ -100,6 +100,8 @@ TreeCost tree_cost(const Hyper& h, const Tree& t, const std::vector<char>& slice
 Tree greedy_tree(const Hyper& h, const std::vector<char>& sliced, uint64_t seed, double temperature);
 Tree bisect_tree(const Hyper& h, uint64_t seed, double imbalance, int leaf_group);
 std::vector<int> choose_slices(const Hyper& h, const Tree& t, int cap_log2, bool* feasible);
+// Local re-optimisation of t (sliced labels removed); returns the number of regions improved.
+int reconfigure(const Hyper& h, Tree* t, const std::vector<char>& sliced, int cap_log2, int max_frontier, int sweeps);
 
 // ---------------------------------------------------------------- plan
 struct Step {

@@ -51,7 +51,7 @@ cudaError_t launch_reduce_splits(const void* part, int splits, size_t n, void* C
 
 // Skinny steps (see skinny.cu).  rows: C = S x G^T for a small operand S of
 // ns <= 16 rows; output element (h, s, g) at h*ns*ng + s*s_stride + g*g_stride.
-// dot: M, N <= 4; always writes FP32 partials [splits][batch][M][N].
+// dot: M, N <= 8; always writes FP32 partials [splits][batch][M][N].
 cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, void* acc, void* part, int splits,
                               int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
                               cudaStream_t st);

@@ -10,7 +10,11 @@
 //     vertices, indices = hyperedges) with Fiduccia-Mattheyses refinement,
 //     finished by the greedy on small groups;
 //   * choose_slices: repeatedly slices the index whose removal most lowers the
-//     largest intermediate (then the total FLOPs) until the cap holds.
+//     largest intermediate (then the total FLOPs) until the cap holds;
+//   * reconfigure: local re-optimisation of a tree: every node's subtree is cut
+//     into at most 8 frontier subtrees whose optimal contraction order (FLOPs,
+//     with the intermediate-size cap as a constraint) is found by dynamic
+//     programming over subsets and swapped in when cheaper.
 // Labels may be hyperedges (batch labels sit on every projection leaf); a
 // label stays open while a tensor outside the subtree still holds it or it is
 // an output label.
@@ -19,6 +23,7 @@
 #include <cmath>
 #include <limits>
 #include <queue>
+#include <functional>
 #include <random>
 
 #include "internal.h"
@@ -412,6 +417,171 @@ std::vector<int> choose_slices(const Hyper& h, const Tree& t, int cap_log2, bool
   }
   if (tree_cost(h, t, sliced).max_log2 > cap_log2) *feasible = false;
   return chosen;
+}
+
+namespace {
+
+struct Bits256 {
+  uint64_t w[4] = {0, 0, 0, 0};
+  void set(int i) { w[i >> 6] |= uint64_t(1) << (i & 63); }
+  Bits256 operator|(const Bits256& o) const {
+    Bits256 r;
+    for (int i = 0; i < 4; ++i) r.w[i] = w[i] | o.w[i];
+    return r;
+  }
+  Bits256 operator&(const Bits256& o) const {
+    Bits256 r;
+    for (int i = 0; i < 4; ++i) r.w[i] = w[i] & o.w[i];
+    return r;
+  }
+  int count() const { return __builtin_popcountll(w[0]) + __builtin_popcountll(w[1]) + __builtin_popcountll(w[2]) +
+                             __builtin_popcountll(w[3]); }
+};
+
+}  // namespace
+
+int reconfigure(const Hyper& h, Tree* t, const std::vector<char>& sliced, int cap_log2, int max_frontier,
+                int sweeps) {
+  const int L = t->n_leaves;
+  const int N = L + (int)t->nodes.size();
+  if (t->nodes.empty()) return 0;
+  int improved = 0;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    std::vector<LC> labs;
+    node_labels(h, *t, sliced, &labs, nullptr);
+    std::vector<int> left(N, -1), right(N, -1);
+    for (int j = 0; j < (int)t->nodes.size(); ++j) {
+      left[L + j] = t->nodes[j].first;
+      right[L + j] = t->nodes[j].second;
+    }
+    const int root = N - 1;
+    int changed = 0;
+    // visit internal nodes top-down so re-optimised regions are used as given
+    for (int v = N - 1; v >= L; --v) {
+      // frontier: expand the largest internal member until max_frontier members
+      std::vector<int> front = {left[v], right[v]};
+      std::vector<int> inner = {v};
+      while ((int)front.size() < max_frontier) {
+        int bi = -1;
+        size_t bs = 0;
+        for (int i = 0; i < (int)front.size(); ++i)
+          if (front[i] >= L && (bi < 0 || labs[front[i]].size() > bs)) {
+            bi = i;
+            bs = labs[front[i]].size();
+          }
+        if (bi < 0) break;
+        const int u = front[bi];
+        inner.push_back(u);
+        front[bi] = left[u];
+        front.push_back(right[u]);
+      }
+      const int k = (int)front.size();
+      if (k < 3) continue;
+      // local label bitsets
+      std::vector<int> ids;
+      for (int f : front)
+        for (auto& e : labs[f]) ids.push_back(e.first);
+      std::sort(ids.begin(), ids.end());
+      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+      if (ids.size() > 256) continue;
+      auto bit_of = [&](int l) { return int(std::lower_bound(ids.begin(), ids.end(), l) - ids.begin()); };
+      std::vector<Bits256> in1(k);
+      for (int i = 0; i < k; ++i)
+        for (auto& e : labs[front[i]]) in1[i].set(bit_of(e.first));
+      Bits256 vout;
+      for (auto& e : labs[v]) {
+        auto it = std::lower_bound(ids.begin(), ids.end(), e.first);
+        if (it != ids.end() && *it == e.first) vout.set(int(it - ids.begin()));
+      }
+      const int full = (1 << k) - 1;
+      std::vector<Bits256> in(1 << k), open(1 << k);
+      for (int S = 1; S <= full; ++S) {
+        const int low = __builtin_ctz(S);
+        in[S] = in[S & (S - 1)] | in1[low];
+      }
+      for (int S = 1; S <= full; ++S) open[S] = in[S] & (in[full & ~S] | vout);
+      std::vector<double> cost(1 << k, 1e300);
+      std::vector<int> split(1 << k, 0);
+      for (int i = 0; i < k; ++i) cost[1 << i] = 0;
+      for (int S = 1; S <= full; ++S) {
+        if (__builtin_popcount(S) < 2) continue;
+        if (S != full && open[S].count() > cap_log2) continue;
+        const int low = S & -S;
+        for (int A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+          if (!(A & low)) continue;
+          const int B = S ^ A;
+          if (cost[A] >= 1e299 || cost[B] >= 1e299) continue;
+          const double c = cost[A] + cost[B] + 8.0 * std::ldexp(1.0, (open[A] | open[B]).count());
+          if (c < cost[S]) {
+            cost[S] = c;
+            split[S] = A;
+          }
+        }
+      }
+      // current cost of the region between v and its frontier
+      double cur = 0;
+      for (int u : inner) {
+        LC uu;
+        merge_lc(labs[left[u]], labs[right[u]], &uu);
+        cur += 8.0 * std::ldexp(1.0, (int)uu.size());
+      }
+      if (!(cost[full] < cur * (1.0 - 1e-9))) continue;
+      // rebuild the region with the inner node ids (v stays the region's root)
+      std::vector<int> pool(inner.begin() + 1, inner.end());
+      std::function<int(int, int)> build = [&](int S, int as) -> int {
+        if (__builtin_popcount(S) == 1) return front[__builtin_ctz(S)];
+        const int A = split[S], B = S ^ A;
+        const int node = as >= 0 ? as : pool.back();
+        if (as < 0) pool.pop_back();
+        const int a = build(A, -1), b = build(B, -1);
+        left[node] = a;
+        right[node] = b;
+        return node;
+      };
+      build(full, v);
+      ++changed;
+      // label sets of rebuilt inner nodes: recompute the region bottom-up
+      std::function<void(int)> relabel = [&](int u) {
+        if (u < L) return;
+        relabel(left[u]);
+        relabel(right[u]);
+        LC uu;
+        merge_lc(labs[left[u]], labs[right[u]], &uu);
+        close_lc(h, uu, &labs[u]);
+      };
+      relabel(v);
+    }
+    if (!changed) break;
+    improved += changed;
+    // re-linearise in post order from the root
+    Tree nt;
+    nt.n_leaves = L;
+    std::vector<int> newid(N, -1);
+    for (int i = 0; i < L; ++i) newid[i] = i;
+    std::vector<std::pair<int, int>> stack;  // (node, state)
+    stack.push_back({root, 0});
+    while (!stack.empty()) {
+      auto& top = stack.back();
+      const int u = top.first;
+      if (u < L) {
+        stack.pop_back();
+        continue;
+      }
+      if (top.second == 0) {
+        top.second = 1;
+        stack.push_back({left[u], 0});
+      } else if (top.second == 1) {
+        top.second = 2;
+        stack.push_back({right[u], 0});
+      } else {
+        newid[u] = L + (int)nt.nodes.size();
+        nt.nodes.push_back({newid[left[u]], newid[right[u]]});
+        stack.pop_back();
+      }
+    }
+    *t = nt;
+  }
+  return improved;
 }
 
 }  // namespace tnq

@@ -342,13 +342,19 @@ tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, c
   const int NC = (int)cands.size();
   std::vector<double> totals(NC, -1.0);
   std::vector<std::vector<int>> slices(NC);
+  // Per candidate: re-optimise the unsliced tree locally, choose the slices,
+  // then re-optimise again under the size cap with the sliced labels fixed.
   auto eval = [&](int i) {
     bool feas = false;
+    reconfigure(h, &cands[i], std::vector<char>(h.n_labels, 0), 64, 8, 4);
     std::vector<int> sl = choose_slices(h, cands[i], o.max_intermediate_log2, &feas);
     if (!feas) return;
     std::vector<char> sv(h.n_labels, 0);
     for (int l : sl) sv[l] = 1;
+    // local re-optimisation of the sliced tree under the same size cap
+    reconfigure(h, &cands[i], sv, o.max_intermediate_log2, 8, 6);
     TreeCost tc = tree_cost(h, cands[i], sv);
+    if (tc.max_log2 > o.max_intermediate_log2) return;
     totals[i] = tc.flops * std::ldexp(1.0, (int)sl.size());
     slices[i] = sl;
   };

@@ -10,7 +10,9 @@
 //                 operand, the small operand and a K slice of G are staged in
 //                 shared memory by coalesced loads; output strides make the
 //                 same kernel serve both "small M" and "small N".
-//   dot kernel:   M, N <= 4 and long K: every thread walks its own part of K
+//   rows kernel, short K (<= 32): each thread loads its row of the large operand
+//                 into registers with 16-byte loads (no staging);
+//   dot kernel:   M, N <= 8 and long K: every thread walks its own part of K
 //                 with 16-byte loads and keeps the M x N sums in registers; the
 //                 CTA reduces them and writes one partial per CTA.
 #include <algorithm>
@@ -96,25 +98,28 @@ __global__ void __launch_bounds__(RW_THREADS) cgemm_rows_kernel(
 
 constexpr int DOT_THREADS = 256;
 
+// MX x MX complex sums per thread (MX = 4 or 8): register accumulators over the
+// thread's part of K, then a fixed-order reduction over the CTA.
+template <int MX>
 __global__ void __launch_bounds__(DOT_THREADS) cdot_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
                                                            float2* __restrict__ part, int M, int N, int K,
-                                                           int kchunk, int splits) {
-  __shared__ float red[DOT_THREADS / 32][32];
+                                                           int kchunk) {
+  __shared__ float red[DOT_THREADS / 32][2 * MX * MX];
   const int split = blockIdx.x, h = blockIdx.y;
   const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
   const float2* Ah = A + size_t(h) * M * K;
   const float2* Bh = B + size_t(h) * N * K;
-  float cr[4][4], ci[4][4];
+  float cr[MX][MX], ci[MX][MX];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MX; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) cr[i][j] = ci[i][j] = 0.f;
+    for (int j = 0; j < MX; ++j) cr[i][j] = ci[i][j] = 0.f;
   // two complex values per 16-byte load (kbeg is even because kchunk is)
   for (int k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * DOT_THREADS) {
     const bool two = k + 1 < kend;
-    float4 a[4], b[4];
+    float4 a[MX], b[MX];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < MX; ++i) {
       a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       b[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i < M) {
@@ -127,9 +132,9 @@ __global__ void __launch_bounds__(DOT_THREADS) cdot_kernel(const float2* __restr
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MX; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < MX; ++j) {
         cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
         cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
         ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
@@ -140,12 +145,11 @@ __global__ void __launch_bounds__(DOT_THREADS) cdot_kernel(const float2* __restr
         ci[i][j] = fmaf(a[i].w, b[j].z, ci[i][j]);
       }
   }
-  // reduce the 32 sums (16 re, 16 im) over the CTA in a fixed order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MX; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < MX; ++j) {
       float r = cr[i][j], im = ci[i][j];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -153,21 +157,80 @@ __global__ void __launch_bounds__(DOT_THREADS) cdot_kernel(const float2* __restr
         im += __shfl_xor_sync(0xffffffffu, im, off);
       }
       if (lane == 0) {
-        red[warp][2 * (i * 4 + j)] = r;
-        red[warp][2 * (i * 4 + j) + 1] = im;
+        red[warp][2 * (i * MX + j)] = r;
+        red[warp][2 * (i * MX + j) + 1] = im;
       }
     }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  for (int q = threadIdx.x; q < 2 * MX * MX; q += DOT_THREADS) {
     float v = 0.f;
-    for (int w = 0; w < DOT_THREADS / 32; ++w) v += red[w][threadIdx.x];
-    const int ij = threadIdx.x >> 1, i = ij >> 2, j = ij & 3;
+    for (int w = 0; w < DOT_THREADS / 32; ++w) v += red[w][q];
+    const int ij = q >> 1, i = ij / MX, j = ij % MX;
     if (i < M && j < N) {
       float* dst = reinterpret_cast<float*>(part + (size_t(split) * gridDim.y + h) * M * N + size_t(i) * N + j);
-      dst[threadIdx.x & 1] = v;
+      dst[q & 1] = v;
     }
   }
-  (void)splits;
+}
+
+// Small operand of ns <= 16 rows and K <= 32: each thread owns one row of the
+// large operand and reads it with 16-byte loads straight into registers.
+template <int KMAX>
+__global__ void __launch_bounds__(256) cgemm_rows_regk_kernel(const float2* __restrict__ S, const float2* __restrict__ G,
+                                                              float2* __restrict__ C, double2* __restrict__ acc, int ns,
+                                                              int ng, int K, int batch, long long s_stride,
+                                                              long long g_stride, int tiles_g) {
+  __shared__ float2 Ss[RW_SMAX][KMAX];
+  const int tile = int(blockIdx.x % tiles_g);
+  const int h = int(blockIdx.x / tiles_g);
+  const float2* Sh = S + size_t(h) * ns * K;
+  for (int i = threadIdx.x; i < RW_SMAX * KMAX; i += blockDim.x) {
+    const int r = i / KMAX, kk = i % KMAX;
+    Ss[r][kk] = (r < ns && kk < K) ? Sh[size_t(r) * K + kk] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int g = tile * blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  const float2* row = G + size_t(h) * ng * K + size_t(g) * K;
+  float2 gv[KMAX];
+  if ((K & 1) == 0) {
+#pragma unroll
+    for (int kk = 0; kk < KMAX; kk += 2)
+      if (kk < K) {
+        const float4 v = *reinterpret_cast<const float4*>(row + kk);
+        gv[kk] = make_float2(v.x, v.y);
+        gv[kk + 1] = make_float2(v.z, v.w);
+      }
+  } else {
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk)
+      if (kk < K) gv[kk] = row[kk];
+  }
+  const size_t hbase = size_t(h) * ns * ng;
+#pragma unroll
+  for (int s = 0; s < RW_SMAX; ++s) {
+    if (s >= ns) break;
+    float ar = 0.f, ai = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk) {
+      if (kk < K) {
+        const float2 a = Ss[s][kk], b = gv[kk];
+        ar = fmaf(a.x, b.x, ar);
+        ar = fmaf(-a.y, b.y, ar);
+        ai = fmaf(a.x, b.y, ai);
+        ai = fmaf(a.y, b.x, ai);
+      }
+    }
+    const size_t o = hbase + size_t(s) * s_stride + size_t(g) * g_stride;
+    if (acc) {
+      double2 v = acc[o];
+      v.x += ar;
+      v.y += ai;
+      acc[o] = v;
+    } else {
+      C[o] = make_float2(ar, ai);
+    }
+  }
 }
 
 }  // namespace
@@ -176,6 +239,23 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
                               int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
                               cudaStream_t st) {
   if (ns < 1 || ns > RW_SMAX || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
+  if (K <= 32 && splits == 1) {
+    // short rows: register-resident row of the large operand
+    const long long tg = (ng + 255) / 256;
+    if (tg * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const dim3 g2{unsigned(tg * batch), 1u, 1u};
+    const float2* Sp = reinterpret_cast<const float2*>(Ssmall);
+    const float2* Gp = reinterpret_cast<const float2*>(Gbig);
+    float2* Cp = reinterpret_cast<float2*>(C);
+    double2* Ap = reinterpret_cast<double2*>(acc);
+    if (K <= 8)
+      cgemm_rows_regk_kernel<8><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
+    else if (K <= 16)
+      cgemm_rows_regk_kernel<16><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
+    else
+      cgemm_rows_regk_kernel<32><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
+    return cudaGetLastError();
+  }
   const long long tiles_g = (ng + RW_THREADS - 1) / RW_THREADS;
   if (tiles_g * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   int kchunk = ((K + splits - 1) / splits + RW_KC - 1) / RW_KC * RW_KC;
@@ -189,12 +269,17 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
 
 cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, int M, int N, int K, int batch,
                         cudaStream_t st) {
-  if (M < 1 || M > 4 || N < 1 || N > 4 || splits < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
+  if (M < 1 || M > 8 || N < 1 || N > 8 || splits < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + 1) & ~1;
   dim3 grid{unsigned(splits), unsigned(batch), 1u};
-  cdot_kernel<<<grid, DOT_THREADS, 0, st>>>(reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(B),
-                                            reinterpret_cast<float2*>(part), M, N, K, kchunk, splits);
+  const float2* Ap = reinterpret_cast<const float2*>(A);
+  const float2* Bp = reinterpret_cast<const float2*>(B);
+  float2* Pp = reinterpret_cast<float2*>(part);
+  if (M <= 4 && N <= 4)
+    cdot_kernel<4><<<grid, DOT_THREADS, 0, st>>>(Ap, Bp, Pp, M, N, K, kchunk);
+  else
+    cdot_kernel<8><<<grid, DOT_THREADS, 0, st>>>(Ap, Bp, Pp, M, N, K, kchunk);
   return cudaGetLastError();
 }
 

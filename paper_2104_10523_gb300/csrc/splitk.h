@@ -19,8 +19,8 @@ constexpr double kPartialCapElems = 1 << 26;  // complex64 partial elements (512
 // tensor-core modes: they are bandwidth-bound and a 128-row MMA tile would idle.
 inline bool skinny(int nM, int nN) { return nM <= 4 || nN <= 4; }
 
-// Tiny outputs (M, N <= 4) with a long contracted dimension: the dot kernel.
-inline bool use_dot(int nM, int nN, int nK) { return nM <= 2 && nN <= 2 && nK >= 10; }
+// Tiny outputs (M, N <= 8) with a long contracted dimension: the dot kernel.
+inline bool use_dot(int nM, int nN, int nK) { return nM <= 3 && nN <= 3 && nK >= 10; }
 
 // tiles: CTAs without splitting; kunits: K extent in units the split may cut
 // (SIMT: 16-element K slices; tensor cores: 128-byte K blocks); min_units: the
@@ -37,8 +37,10 @@ inline int simt_splits(int nH, int nM, int nN, int nK) {
   return split_factor(tiles, std::ceil(std::ldexp(1.0, nK) / 16.0), 16.0, std::ldexp(1.0, nH + nM + nN));
 }
 
-// rows kernel: 128 rows of the large operand per CTA, K staged 32 at a time.
+// rows kernel: 128 rows of the large operand per CTA, K staged 32 at a time;
+// short K (<= 32) runs unsplit with the row in registers.
 inline int rows_splits(int nH, int nM, int nN, int nK) {
+  if (nK <= 5) return 1;
   int big = std::max(nM, nN);
   double tiles = std::ldexp(1.0, nH) * std::ceil(std::ldexp(1.0, big) / 128.0);
   return split_factor(tiles, std::ceil(std::ldexp(1.0, nK) / 32.0), 8.0, std::ldexp(1.0, nH + nM + nN));
