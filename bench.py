@@ -192,6 +192,10 @@ def main():
     ctx.bind(plan)
     info = plan.info
     stream = ctx.stream
+    t_tune = time.perf_counter()
+    n_tc, n_cc = tnq.tnq_plan_autotune(ctx.h, plan.h, 3)
+    t_tune = time.perf_counter() - t_tune
+    log(f"autotune: {n_tc} steps on tensor cores, {n_cc} on CUDA cores, {t_tune:.1f} s")
 
     def batch(i):
         start = ((rank * (a.steps + a.warmup) + i) * B) % WORKLOAD["n_bitstrings"]
@@ -287,7 +291,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": a.precision, "data": "synthetic",
         "config": {"workload": workload_desc(a), "bitstrings_per_step": B, "slices": 2 ** info["n_sliced"],
                    "max_intermediate_log2": info["max_log2"], "flops_per_step": flops_step,
-                   "path_search_s": round(t_plan, 2), "l2": "working set larger than L2 (intermediates up to "
+                   "path_search_s": round(t_plan, 2), "autotune_s": round(t_tune, 2),
+                   "autotuned_steps": {"tensor_core": n_tc, "cuda_core": n_cc}, "l2": "working set larger than L2 (intermediates up to "
                    f"2^{info['max_log2']} x 8 B)", "parallelism": f"dp{world} (independent bitstrings)"},
         "contraction_tflops": tflops,
         "roofline": roofline,

@@ -210,6 +210,15 @@ tnq_status tnq_contract_pair(tnq_ctx* ctx, const void* A, int ra, const int* a_l
 tnq_status tnq_contract_pair_noalloc(tnq_ctx* ctx, const void* A, int ra, const int* a_labels, const void* B,
                                      int rb, const int* b_labels, void* C, int rc, const int* c_labels);
 
+/* Autotune a bound plan for the context's precision: every step that could run
+ * on the tensor cores is timed (CUDA events, best of `reps` after a warm-up run,
+ * on the plan's workspace) both there and on the CUDA cores (row-streaming,
+ * dot or tiled FP32 kernel), and the faster choice is kept in the plan for
+ * that precision; later calls at that precision follow it (and re-capture
+ * their graph).  Results are unchanged in meaning (each choice meets the
+ * precision's bound).  Optional outputs: steps placed on each kind of core. */
+tnq_status tnq_plan_autotune(tnq_ctx* ctx, tnq_plan* p, int reps, int* n_tensor_core, int* n_cuda_core);
+
 /* Replay full batches from a CUDA graph (1, the default) or launch every kernel
  * directly (0).  With graphs on, the first full batch of a plan at a given
  * precision captures every slice and step of one batch into a graph (on a

@@ -379,6 +379,12 @@ tnq_status tnq_plan_get_candidates(const tnq_plan* pp, double* flops, double* pr
   return TNQ_OK;
 }
 
+tnq_status tnq_plan_autotune(tnq_ctx* c, tnq_plan* p, int reps, int* n_tensor_core, int* n_cuda_core) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (reps < 1 || reps > 100) return fail(TNQ_ERR_INVALID_ARG, "reps must be in [1, 100]");
+  return exec_autotune(&c->c, &p->p, reps, n_tensor_core, n_cuda_core);
+}
+
 tnq_status tnq_ctx_set_graphs(tnq_ctx* c, int enable) {
   if (!c) return fail(TNQ_ERR_INVALID_ARG, "NULL context");
   c->c.use_graphs = enable != 0;

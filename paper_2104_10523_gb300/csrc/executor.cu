@@ -117,28 +117,66 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
                          const void* b_src, const std::vector<int>& b_labels, bool perm_b,
                          const std::vector<int>& a_req, const std::vector<int>& b_req,
                          const std::vector<int>& slice_labels, int slice_id, int nH, int nM, int nN, int nK,
-                         char* scratch_a, char* scratch_b, void* C, void* acc, int* err, void* part) {
+                         char* scratch_a, char* scratch_b, void* C, void* acc, int* err, void* part,
+                         int choice = -1) {
   // Small, skinny or K-degenerate steps run on the CUDA cores in FP32 whatever
-  // the mode: they are launch- or bandwidth-bound and a tensor-core tile would idle.
+  // the mode: they are launch- or bandwidth-bound and a tensor-core tile would
+  // idle.  An autotuned choice (0 CUDA cores, 1 tensor cores) overrides the rule.
   const double work = std::ldexp(1.0, nH + nM + nN + nK);
-  const bool use_tc = ctx->precision != TNQ_PREC_FP32 && !skinny(nM, nN) &&
-                      tc_gemm_supported(1 << nM, 1 << nN, 1 << nK, ctx->precision) && work >= ctx->tc_min_work;
+  const bool tc_ok = ctx->precision != TNQ_PREC_FP32 && tc_gemm_supported(1 << nM, 1 << nN, 1 << nK, ctx->precision);
+  const bool use_tc = choice == 1 ? tc_ok
+                      : choice == 0 ? false
+                                    : tc_ok && !skinny(nM, nN, nK) && work >= ctx->tc_min_work;
   const size_t out_elems = size_t(1) << (nH + nM + nN);
   const int prec = use_tc ? ctx->precision : TNQ_PREC_FP32;
   StepOperands op;
   PermDesc d;
   const int ns = (int)slice_labels.size();
-  if (!use_tc && (skinny(nM, nN) || use_dot(nM, nN, nK)) && part) {
+  if (!use_tc && (rows_capable(nM, nN) || use_dot(nM, nN, nK)) && part) {
     // bandwidth-bound skinny step: complex64 operands in [h][m|n][k] order
-    if (perm_a) {
+    // The large operand of a short-K rows step is read in place (fused gather)
+    // instead of being permuted first.
+    const bool small_is_a = nM <= nN;
+    const bool gather = !use_dot(nM, nN, nK) && nK <= 5 && (small_is_a ? perm_b : perm_a);
+    if (perm_a && !(gather && !small_is_a)) {
       build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(),
                       ns, PM_C64, nK, &d);
       TNQ_CUDA(perm(ctx, d, a_src, scratch_a, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)a_req.size())));
     }
-    if (perm_b) {
+    if (perm_b && !(gather && small_is_a)) {
       build_perm_desc(b_labels.data(), (int)b_labels.size(), b_req.data(), (int)b_req.size(), slice_labels.data(),
                       ns, PM_C64, nK, &d);
       TNQ_CUDA(perm(ctx, d, b_src, scratch_b, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)b_req.size())));
+    }
+    if (gather) {
+      // large operand: required order [K][rows][H]; find each bit in its stored labels
+      const std::vector<int>& src_l = small_is_a ? b_labels : a_labels;
+      const std::vector<int>& req = small_is_a ? b_req : a_req;
+      auto spos = [&](int l) { return int(std::find(src_l.begin(), src_l.end(), l) - src_l.begin()); };
+      GatherDesc gd;
+      gd.nk = nK;
+      for (int j = 0; j < nK; ++j) gd.kpos[j] = spos(req[j]);
+      gd.nrow = (int)req.size() - nK;
+      for (int j = 0; j < gd.nrow; ++j) gd.rowpos[j] = spos(req[nK + j]);
+      gd.n_slice = ns;
+      for (int j = 0; j < 32; ++j) gd.slice_src[j] = j < ns ? spos(slice_labels[j]) : -1;
+      for (int j = 0; j < ns; ++j)
+        if (gd.slice_src[j] >= (int)src_l.size()) gd.slice_src[j] = -1;
+      const int M = 1 << nM, N = 1 << nN, K = 1 << nK, H = 1 << nH;
+      const void* Ssm = small_is_a ? (perm_a ? (const void*)scratch_a : a_src) : (perm_b ? (const void*)scratch_b : b_src);
+      const void* Gs = small_is_a ? b_src : a_src;
+      KernelRecord r{4, ctx->cur_step, nH, nM, nN, nK, 8.0 * work,
+                     8.0 * (std::ldexp(1.0, nH + nM + nK) + std::ldexp(1.0, nH + nN + nK) +
+                            (acc ? 2.0 : 1.0) * std::ldexp(1.0, nH + nM + nN)),
+                     0.f};
+      int slot = timing_begin(ctx);
+      cudaError_t e = small_is_a
+                          ? launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, M, N, K, H, N, 1, slice_id, ctx->stream)
+                          : launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, N, M, K, H, 1, N, slice_id, ctx->stream);
+      timing_end(ctx, slot, r);
+      TNQ_CUDA(e);
+      ctx->launches++;
+      return TNQ_OK;
     }
     const void* A = perm_a ? (const void*)scratch_a : a_src;
     const void* B = perm_b ? (const void*)scratch_b : b_src;
@@ -255,24 +293,29 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
   return TNQ_OK;
 }
 
+tnq_status run_step(Ctx* ctx, Plan* p, size_t si, int slice_id, char* ws, int choice) {
+  auto& s = p->steps[si];
+  auto& ta = p->tensors[s.a];
+  auto& tb = p->tensors[s.b];
+  void* acc = s.out == p->root ? (void*)(ws + p->ws_acc) : nullptr;
+  void* C = s.out == p->root ? nullptr : (void*)(ws + p->tensors[s.out].offset);
+  return run_gemm_step(ctx, ws + ta.offset, ta.labels, s.perm_a, ws + tb.offset, tb.labels, s.perm_b, s.a_req,
+                       s.b_req, p->slice_labels, slice_id, s.nH, s.nM, s.nN, s.nK, ws + p->ws_scratch_a,
+                       ws + p->ws_scratch_b, C, acc, reinterpret_cast<int*>(ws + p->ws_misc + 4),
+                       ws + p->ws_partial, choice);
+}
+
 tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws) {
+  const bool tuned = p->tuned_precision == ctx->precision && p->kernel_choice.size() == p->steps.size();
   for (size_t si = 0; si < p->steps.size(); ++si) {
-    auto& s = p->steps[si];
     ctx->cur_step = (int)si;
-    auto& ta = p->tensors[s.a];
-    auto& tb = p->tensors[s.b];
-    void* acc = s.out == p->root ? (void*)(ws + p->ws_acc) : nullptr;
-    void* C = s.out == p->root ? nullptr : (void*)(ws + p->tensors[s.out].offset);
-    tnq_status st = run_gemm_step(ctx, ws + ta.offset, ta.labels, s.perm_a,
-                                  ws + tb.offset, tb.labels, s.perm_b,
-                                  s.a_req, s.b_req, p->slice_labels, slice_id, s.nH, s.nM, s.nN, s.nK,
-                                  ws + p->ws_scratch_a, ws + p->ws_scratch_b, C, acc,
-                                  reinterpret_cast<int*>(ws + p->ws_misc + 4), ws + p->ws_partial);
+    tnq_status st = run_step(ctx, p, si, slice_id, ws, tuned ? p->kernel_choice[si] : -1);
     if (st != TNQ_OK) return st;
   }
   ctx->cur_step = -1;
   return TNQ_OK;
 }
+
 
 }  // namespace
 
@@ -472,6 +515,67 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
   }
   if (herr[1]) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired; results are invalid");
   if (herr[0]) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  return TNQ_OK;
+}
+
+tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda) {
+  if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
+  TNQ_CUDA(cudaSetDevice(ctx->device));
+  if (ctx->precision != TNQ_PREC_FP32) TNQ_CUDA(tc_gemm_prepare());
+  char* ws = static_cast<char*>(p->bound_ws);
+  const size_t n = p->steps.size();
+  std::vector<int8_t> choice(n, -1);
+  cudaEvent_t e0, e1;
+  TNQ_CUDA(cudaEventCreate(&e0));
+  TNQ_CUDA(cudaEventCreate(&e1));
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  int ntc = 0, ncc = 0;
+  tnq_status result = TNQ_OK;
+  for (size_t si = 0; si < n && result == TNQ_OK; ++si) {
+    const Step& s = p->steps[si];
+    const bool tc_ok = ctx->precision != TNQ_PREC_FP32 &&
+                       tc_gemm_supported(1 << s.nM, 1 << s.nN, 1 << s.nK, ctx->precision) &&
+                       s.nM + s.nN + s.nK + s.nH >= 12;
+    if (!tc_ok) continue;  // one candidate only
+    float best = 0;
+    int pick = -1;
+    for (int c = 0; c < 2 && result == TNQ_OK; ++c) {
+      float tmin = 1e30f;
+      for (int r = 0; r < reps + 1; ++r) {  // first run warms up
+        cudaEventRecord(e0, ctx->stream);
+        result = run_step(ctx, p, si, 0, ws, c);
+        cudaEventRecord(e1, ctx->stream);
+        if (result != TNQ_OK) break;
+        cudaError_t er = cudaEventSynchronize(e1);
+        if (er != cudaSuccess) {
+          result = cuda_fail(er, "autotune");
+          break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) tmin = std::min(tmin, ms);
+      }
+      if (pick < 0 || tmin < best) {
+        pick = c;
+        best = tmin;
+      }
+    }
+    choice[si] = (int8_t)pick;
+    (pick == 1 ? ntc : ncc)++;
+  }
+  ctx->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != TNQ_OK) return result;
+  int herr = 0;
+  TNQ_CUDA(cudaMemcpy(&herr, ws + p->ws_misc + 4, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired during autotuning");
+  p->kernel_choice = choice;
+  p->tuned_precision = ctx->precision;
+  plan_release_graph(p);
+  if (n_tc) *n_tc = ntc;
+  if (n_cuda) *n_cuda = ncc;
   return TNQ_OK;
 }
 

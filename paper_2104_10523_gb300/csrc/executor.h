@@ -35,6 +35,7 @@ struct Ctx {
 };
 
 void plan_release_graph(Plan* p);
+tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda);
 
 // Timing helpers: bracket a launch when ctx->timing is set.
 int timing_begin(Ctx* ctx);

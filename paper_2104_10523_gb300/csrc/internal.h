@@ -149,6 +149,10 @@ struct Plan {
   // time (learned ranking, else -1), the flop-minimal one and the chosen one
   std::vector<double> cand_flops, cand_pred;
   int cand_flopmin = -1, cand_chosen = -1;
+  // autotuned kernel choice per step (for tuned_precision): -1 default rule,
+  // 0 CUDA cores, 1 tensor cores
+  std::vector<int8_t> kernel_choice;
+  int tuned_precision = -1;
   // CUDA graph of one full batch (every slice and step), per precision
   void* graph_exec = nullptr;     // cudaGraphExec_t
   int graph_precision = -1;

@@ -34,8 +34,8 @@ void build_perm_desc(const int* src_labels, int src_rank, const int* dst_labels,
   for (int p = 0; p < dst_rank; ++p) s_of_d[p] = src_pos(dst_labels[p]);
   for (int j = 0; j < n_slice; ++j) d->slice_src[j] = src_pos(slice_labels[j]);
   for (int j = n_slice; j < 32; ++j) d->slice_src[j] = -1;
-  // tile: lowest destination bits and lowest source bits, grown until 10 bits
-  int target = std::min(dst_rank, 10);
+  // tile: lowest destination bits and lowest source bits, grown until 11 bits
+  int target = std::min(dst_rank, 11);
   std::vector<char> in_tile(dst_rank, 0);
   int u = 0, a = 0, b = 0;
   std::vector<int> d_of_s(src_rank, -1);
@@ -159,10 +159,10 @@ constexpr int PERM_THREADS = 256;
 
 __global__ void __launch_bounds__(PERM_THREADS) permute_kernel(const PermDesc d, const float2* __restrict__ src,
                                                                void* dst0, void* dst1, int slice_id) {
-  __shared__ float2 tile[1024];
-  __shared__ uint32_t srcoff[1024];
-  __shared__ uint32_t dstoff[1024];
-  __shared__ uint16_t eidx[1024];
+  __shared__ float2 tile[2048];
+  __shared__ uint32_t srcoff[2048];
+  __shared__ uint32_t dstoff[2048];
+  __shared__ uint16_t eidx[2048];
   const int T = 1 << d.u;
   for (int e = threadIdx.x; e < T; e += blockDim.x) {
     uint32_t s = 0, o = 0, ei = 0;
@@ -195,9 +195,168 @@ __global__ void __launch_bounds__(PERM_THREADS) permute_kernel(const PermDesc d,
   }
 }
 
+// Vectorised variant: pairs of elements adjacent in the source (tile bit 0 is
+// source bit 0) are loaded with one 16-byte load, pairs adjacent in the
+// destination (tile bit 0 in destination order is destination bit 0) are
+// stored with one 16-byte store (8 bytes for BF16 formats).  The shared tile is
+// XOR-swizzled on bits 1-3 by higher bits so the transposed reads of a
+// half-warp spread over the banks while pairs stay adjacent.
+__device__ __forceinline__ uint32_t swz(uint32_t e) { return e ^ ((((e >> 4) ^ (e >> 8)) & 7u) << 1); }
+
+__device__ __forceinline__ void write_pair(const PermDesc& d, void* dst0, void* dst1, size_t o, float2 v0, float2 v1) {
+  switch (d.mode) {
+    case PM_C64:
+      *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst0) + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+      break;
+    case PM_B_TF32: {
+      *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst0) + o) =
+          make_float4(tf32_round(v0.x), tf32_round(v0.y), tf32_round(v1.x), tf32_round(v1.y));
+      break;
+    }
+    case PM_B_TF32X3: {
+      const float h0 = tf32_round(v0.x), h1 = tf32_round(v0.y), h2 = tf32_round(v1.x), h3 = tf32_round(v1.y);
+      *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst0) + o) = make_float4(h0, h1, h2, h3);
+      *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst1) + o) =
+          make_float4(tf32_round(v0.x - h0), tf32_round(v0.y - h1), tf32_round(v1.x - h2), tf32_round(v1.y - h3));
+      break;
+    }
+    case PM_B_BF16X3: {
+      __nv_bfloat162 a, b, la, lb;
+      a.x = __float2bfloat16_rn(v0.x);
+      a.y = __float2bfloat16_rn(v0.y);
+      b.x = __float2bfloat16_rn(v1.x);
+      b.y = __float2bfloat16_rn(v1.y);
+      la.x = __float2bfloat16_rn(v0.x - __bfloat162float(a.x));
+      la.y = __float2bfloat16_rn(v0.y - __bfloat162float(a.y));
+      lb.x = __float2bfloat16_rn(v1.x - __bfloat162float(b.x));
+      lb.y = __float2bfloat16_rn(v1.y - __bfloat162float(b.y));
+      uint2 hv, lv;
+      hv.x = *reinterpret_cast<uint32_t*>(&a);
+      hv.y = *reinterpret_cast<uint32_t*>(&b);
+      lv.x = *reinterpret_cast<uint32_t*>(&la);
+      lv.y = *reinterpret_cast<uint32_t*>(&lb);
+      *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat162*>(dst0) + o) = hv;
+      *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat162*>(dst1) + o) = lv;
+      break;
+    }
+    default: {  // A' expansion: o and o+1 are consecutive k of the same complex row
+      const size_t K = size_t(1) << d.kbits;
+      const size_t row = o >> d.kbits, k = o & (K - 1);
+      const size_t i0 = (2 * row) * K + k, i1 = (2 * row + 1) * K + k;
+      if (d.mode == PM_AEXP_F32 || d.mode == PM_AEXP_TF32) {
+        float r0 = v0.x, m0 = v0.y, r1 = v1.x, m1 = v1.y;
+        if (d.mode == PM_AEXP_TF32) {
+          r0 = tf32_round(r0);
+          m0 = tf32_round(m0);
+          r1 = tf32_round(r1);
+          m1 = tf32_round(m1);
+        }
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst0) + i0) = make_float4(r0, -m0, r1, -m1);
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst0) + i1) = make_float4(m0, r0, m1, r1);
+      } else if (d.mode == PM_AEXP_TF32X3) {
+        const float r0 = tf32_round(v0.x), m0 = tf32_round(v0.y), r1 = tf32_round(v1.x), m1 = tf32_round(v1.y);
+        const float lr0 = tf32_round(v0.x - r0), lm0 = tf32_round(v0.y - m0), lr1 = tf32_round(v1.x - r1),
+                    lm1 = tf32_round(v1.y - m1);
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst0) + i0) = make_float4(r0, -m0, r1, -m1);
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst0) + i1) = make_float4(m0, r0, m1, r1);
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst1) + i0) = make_float4(lr0, -lm0, lr1, -lm1);
+        *reinterpret_cast<float4*>(reinterpret_cast<float2*>(dst1) + i1) = make_float4(lm0, lr0, lm1, lr1);
+      } else {  // PM_AEXP_BF16X3
+        __nv_bfloat16 r0 = __float2bfloat16_rn(v0.x), m0 = __float2bfloat16_rn(v0.y);
+        __nv_bfloat16 r1 = __float2bfloat16_rn(v1.x), m1 = __float2bfloat16_rn(v1.y);
+        __nv_bfloat16 lr0 = __float2bfloat16_rn(v0.x - __bfloat162float(r0));
+        __nv_bfloat16 lm0 = __float2bfloat16_rn(v0.y - __bfloat162float(m0));
+        __nv_bfloat16 lr1 = __float2bfloat16_rn(v1.x - __bfloat162float(r1));
+        __nv_bfloat16 lm1 = __float2bfloat16_rn(v1.y - __bfloat162float(m1));
+        __nv_bfloat162 p00, p01, p10, p11, q00, q01, q10, q11;
+        p00.x = r0; p00.y = __hneg(m0); p01.x = r1; p01.y = __hneg(m1);     // row (m, re), hi
+        p10.x = m0; p10.y = r0; p11.x = m1; p11.y = r1;                     // row (m, im), hi
+        q00.x = lr0; q00.y = __hneg(lm0); q01.x = lr1; q01.y = __hneg(lm1); // lo parts
+        q10.x = lm0; q10.y = lr0; q11.x = lm1; q11.y = lr1;
+        uint2 w;
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(dst0);
+        __nv_bfloat162* l = reinterpret_cast<__nv_bfloat162*>(dst1);
+        w.x = *reinterpret_cast<uint32_t*>(&p00); w.y = *reinterpret_cast<uint32_t*>(&p01);
+        *reinterpret_cast<uint2*>(h + i0) = w;
+        w.x = *reinterpret_cast<uint32_t*>(&p10); w.y = *reinterpret_cast<uint32_t*>(&p11);
+        *reinterpret_cast<uint2*>(h + i1) = w;
+        w.x = *reinterpret_cast<uint32_t*>(&q00); w.y = *reinterpret_cast<uint32_t*>(&q01);
+        *reinterpret_cast<uint2*>(l + i0) = w;
+        w.x = *reinterpret_cast<uint32_t*>(&q10); w.y = *reinterpret_cast<uint32_t*>(&q11);
+        *reinterpret_cast<uint2*>(l + i1) = w;
+      }
+    }
+  }
+}
+
+constexpr int PV_THREADS = 256;
+
+__global__ void __launch_bounds__(PV_THREADS) permute_vec_kernel(const PermDesc d, const float2* __restrict__ src,
+                                                                 void* dst0, void* dst1, int slice_id) {
+  __shared__ __align__(16) float2 tile[2048];
+  __shared__ uint32_t srcoff[1024];   // per source-order pair
+  __shared__ uint32_t dstoff[1024];   // per destination-order pair
+  __shared__ uint16_t epos[2048];     // per destination-order element: swizzled tile position
+  const int T = 1 << d.u, P = T >> 1;
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {
+    const int e = q << 1;  // even element in source order
+    uint32_t s = 0, o = 0;
+    for (int i = 1; i < d.u; ++i)
+      if ((e >> i) & 1) {
+        s |= 1u << d.tile_src[i];
+        o |= 1u << d.tile_dst_sorted[i];
+      }
+    srcoff[q] = s;
+    dstoff[q] = o;  // destination offset of the even element of pair q in destination order
+  }
+  for (int f = threadIdx.x; f < T; f += blockDim.x) {
+    uint32_t ei = 0;
+    for (int i = 0; i < d.u; ++i)
+      if ((f >> i) & 1) ei |= 1u << d.tile_srcidx_of_dst[i];
+    epos[f] = (uint16_t)swz(ei);
+  }
+  size_t slice_off = 0;
+  for (int j = 0; j < d.n_slice; ++j)
+    if (d.slice_src[j] >= 0 && ((slice_id >> j) & 1)) slice_off |= size_t(1) << d.slice_src[j];
+  __syncthreads();
+  const size_t n_outer = size_t(1) << d.n_outer;
+  for (size_t c = blockIdx.x; c < n_outer; c += gridDim.x) {
+    size_t sb = slice_off, db = 0;
+    for (int k = 0; k < d.n_outer; ++k)
+      if ((c >> k) & 1) {
+        sb |= size_t(1) << d.outer_src[k];
+        db |= size_t(1) << d.outer_dst[k];
+      }
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+      const float4 v = *reinterpret_cast<const float4*>(src + sb + srcoff[q]);
+      *reinterpret_cast<float4*>(tile + swz(uint32_t(q) << 1)) = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+      const int f = q << 1;
+      write_pair(d, dst0, dst1, db + dstoff[q], tile[epos[f]], tile[epos[f + 1]]);
+    }
+    __syncthreads();
+  }
+}
+
+bool perm_vec_ok(const PermDesc& d) {
+  // pairs: source bit 0 and destination bit 0 are both the tile's first bit,
+  // and A' expansions keep a pair inside one row (at least two K elements)
+  if (d.u < 2 || d.tile_src[0] != 0 || d.tile_dst_sorted[0] != 0) return false;
+  if (d.mode >= PM_AEXP_F32 && d.mode <= PM_AEXP_BF16X3 && d.kbits < 1) return false;
+  return true;
+}
+
 cudaError_t launch_permute(const PermDesc& d, const void* src, void* dst0, void* dst1, int slice_id,
                            int sm_count, cudaStream_t st) {
   size_t n_outer = size_t(1) << d.n_outer;
+  if (perm_vec_ok(d)) {
+    size_t grid = std::min<size_t>(n_outer, size_t(sm_count) * 8);
+    permute_vec_kernel<<<(unsigned)grid, PV_THREADS, 0, st>>>(d, reinterpret_cast<const float2*>(src), dst0, dst1,
+                                                             slice_id);
+    return cudaGetLastError();
+  }
   size_t grid = std::min<size_t>(n_outer, size_t(sm_count) * 8);
   permute_kernel<<<(unsigned)grid, PERM_THREADS, 0, st>>>(d, reinterpret_cast<const float2*>(src), dst0,
                                                           dst1, slice_id);

@@ -50,13 +50,28 @@ cudaError_t launch_reduce_splits(const void* part, int splits, size_t n, void* C
                                  cudaStream_t st);
 
 // Skinny steps (see skinny.cu).  rows: C = S x G^T for a small operand S of
-// ns <= 16 rows; output element (h, s, g) at h*ns*ng + s*s_stride + g*g_stride.
+// ns <= 32 rows; output element (h, s, g) at h*ns*ng + s*s_stride + g*g_stride.
 // dot: M, N <= 8; always writes FP32 partials [splits][batch][M][N].
 cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, void* acc, void* part, int splits,
                               int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
                               cudaStream_t st);
 cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, int M, int N, int K, int batch,
                         cudaStream_t st);
+
+// Bit positions (in the large operand's stored layout) of its row index (the
+// N or M bits, then the batch bits) and of its K bits, plus sliced labels.
+struct GatherDesc {
+  int nrow;
+  int rowpos[32];
+  int nk;
+  int kpos[8];
+  int n_slice;
+  int slice_src[32];
+};
+// rows kernel with K <= 32 reading the large operand in place (fused permute).
+cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc,
+                                     int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
+                                     int slice_id, cudaStream_t st);
 
 // Projection leaves: P_q[(b << 1) | x] = [bits[(base+b)*n + q] == x] for b < n_valid, else 0.
 cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_qubits, int batch_log2,

@@ -263,10 +263,10 @@ void step_features(const Plan& p, int precision, std::vector<float>* out) {
   for (size_t i = 0; i < p.steps.size(); ++i) {
     const Step& s = p.steps[i];
     const int work = s.nH + s.nM + s.nN + s.nK;
-    const bool tc = precision != TNQ_PREC_FP32 && !skinny(s.nM, s.nN) &&
+    const bool tc = precision != TNQ_PREC_FP32 && !skinny(s.nM, s.nN, s.nK) &&
                     tc_gemm_supported(1 << s.nM, 1 << s.nN, 1 << s.nK, precision) && work >= 18;
     const bool dot = !tc && use_dot(s.nM, s.nN, s.nK);
-    const bool rows = !tc && !dot && skinny(s.nM, s.nN);
+    const bool rows = !tc && !dot && skinny(s.nM, s.nN, s.nK);
     const bool simt = !tc && !dot && !rows;
     const double bytes = 8.0 * (std::ldexp(1.0, (int)s.a_req.size()) + std::ldexp(1.0, (int)s.b_req.size()) +
                                 std::ldexp(1.0, (int)s.out_labels.size()));

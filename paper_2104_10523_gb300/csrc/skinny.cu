@@ -6,7 +6,7 @@
 // the large operand once; a tiled GEMM would leave most lanes idle.
 //
 //   rows kernel:  C[h][s][g] = sum_k S[h][s][k] G[h][g][k] for a small side of
-//                 at most 16 rows: each thread owns one row g of the large
+//                 at most 32 rows: each thread owns one row g of the large
 //                 operand, the small operand and a K slice of G are staged in
 //                 shared memory by coalesced loads; output strides make the
 //                 same kernel serve both "small M" and "small N".
@@ -25,7 +25,7 @@ namespace {
 
 constexpr int RW_THREADS = 128;  // rows of the large operand per CTA
 constexpr int RW_KC = 32;        // K elements staged per iteration
-constexpr int RW_SMAX = 16;
+constexpr int RW_SMAX = 32;
 
 __global__ void __launch_bounds__(RW_THREADS) cgemm_rows_kernel(
     const float2* __restrict__ S, const float2* __restrict__ G, float2* __restrict__ C, double2* __restrict__ acc,
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(DOT_THREADS) cdot_kernel(const float2* __restr
   }
 }
 
-// Small operand of ns <= 16 rows and K <= 32: each thread owns one row of the
+// Small operand of ns <= 32 rows and K <= 32: each thread owns one row of the
 // large operand and reads it with 16-byte loads straight into registers.
 template <int KMAX>
 __global__ void __launch_bounds__(256) cgemm_rows_regk_kernel(const float2* __restrict__ S, const float2* __restrict__ G,
@@ -233,7 +233,108 @@ __global__ void __launch_bounds__(256) cgemm_rows_regk_kernel(const float2* __re
   }
 }
 
+// As cgemm_rows_regk_kernel, but the large operand is read in its stored bit
+// layout (no separate permute): row g (its N or M index, then batch bits) starts
+// at the source offset sum_j bit_j(g) << rowpos[j], and element k of a row is
+// koff[k] further on.  Leaves with sliced labels add the slice offset.
+template <int KMAX>
+__global__ void __launch_bounds__(256) cgemm_rows_gather_kernel(const float2* __restrict__ S,
+                                                                const float2* __restrict__ G, const GatherDesc gd,
+                                                                float2* __restrict__ C, double2* __restrict__ acc,
+                                                                int ns, int ng, int K, int batch, long long s_stride,
+                                                                long long g_stride, int tiles_g, int slice_id) {
+  __shared__ float2 Ss[RW_SMAX][KMAX];
+  __shared__ uint32_t koff[KMAX];
+  const int tile = int(blockIdx.x % tiles_g);
+  const int h = int(blockIdx.x / tiles_g);
+  const float2* Sh = S + size_t(h) * ns * K;
+  for (int i = threadIdx.x; i < RW_SMAX * KMAX; i += blockDim.x) {
+    const int r = i / KMAX, kk = i % KMAX;
+    Ss[r][kk] = (r < ns && kk < K) ? Sh[size_t(r) * K + kk] : make_float2(0.f, 0.f);
+  }
+  for (int kk = threadIdx.x; kk < KMAX; kk += blockDim.x) {
+    uint32_t o = 0;
+    for (int j = 0; j < gd.nk; ++j)
+      if ((kk >> j) & 1) o |= 1u << gd.kpos[j];
+    koff[kk] = o;
+  }
+  __syncthreads();
+  const int g = tile * blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  // global row index over (g, h): g's bits first, then the batch bits
+  const long long grow = (long long)h * ng + g;
+  size_t base = 0;
+  for (int j = 0; j < gd.nrow; ++j)
+    if ((grow >> j) & 1) base |= size_t(1) << gd.rowpos[j];
+  for (int j = 0; j < gd.n_slice; ++j)
+    if (gd.slice_src[j] >= 0 && ((slice_id >> j) & 1)) base |= size_t(1) << gd.slice_src[j];
+  float2 gv[KMAX];
+  if (gd.nk >= 1 && gd.kpos[0] == 0) {
+    // the lowest K bit is the stored layout's stride-1 bit: pairs (k, k+1) are
+    // adjacent and 16-byte aligned (every other offset bit is >= 1)
+#pragma unroll
+    for (int kk = 0; kk < KMAX; kk += 2)
+      if (kk < K) {
+        const float4 v = *reinterpret_cast<const float4*>(G + base + koff[kk]);
+        gv[kk] = make_float2(v.x, v.y);
+        gv[kk + 1] = make_float2(v.z, v.w);
+      }
+  } else {
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk)
+      if (kk < K) gv[kk] = G[base + koff[kk]];
+  }
+  const size_t hbase = size_t(h) * ns * ng;
+#pragma unroll
+  for (int s = 0; s < RW_SMAX; ++s) {
+    if (s >= ns) break;
+    float ar = 0.f, ai = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk) {
+      if (kk < K) {
+        const float2 a = Ss[s][kk], b = gv[kk];
+        ar = fmaf(a.x, b.x, ar);
+        ar = fmaf(-a.y, b.y, ar);
+        ai = fmaf(a.x, b.y, ai);
+        ai = fmaf(a.y, b.x, ai);
+      }
+    }
+    const size_t o = hbase + size_t(s) * s_stride + size_t(g) * g_stride;
+    if (acc) {
+      double2 v = acc[o];
+      v.x += ar;
+      v.y += ai;
+      acc[o] = v;
+    } else {
+      C[o] = make_float2(ar, ai);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc,
+                                     int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
+                                     int slice_id, cudaStream_t st) {
+  if (ns < 1 || ns > RW_SMAX || K > 32 || gd.nrow > 32 || gd.nk > 5) return cudaErrorInvalidConfiguration;
+  const long long tg = (ng + 255) / 256;
+  if (tg * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const dim3 g2{unsigned(tg * batch), 1u, 1u};
+  const float2* Sp = reinterpret_cast<const float2*>(Ssmall);
+  const float2* Gp = reinterpret_cast<const float2*>(Gsrc);
+  float2* Cp = reinterpret_cast<float2*>(C);
+  double2* Ap = reinterpret_cast<double2*>(acc);
+  if (K <= 8)
+    cgemm_rows_gather_kernel<8><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out,
+                                                    int(tg), slice_id);
+  else if (K <= 16)
+    cgemm_rows_gather_kernel<16><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
+                                                     g_stride_out, int(tg), slice_id);
+  else
+    cgemm_rows_gather_kernel<32><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
+                                                     g_stride_out, int(tg), slice_id);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, void* acc, void* part, int splits,
                               int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,

@@ -17,7 +17,16 @@ constexpr double kPartialCapElems = 1 << 26;  // complex64 partial elements (512
 
 // Skinny steps (few output rows or columns) stay on the CUDA cores even in the
 // tensor-core modes: they are bandwidth-bound and a 128-row MMA tile would idle.
-inline bool skinny(int nM, int nN) { return nM <= 4 || nN <= 4; }
+// Default rule (the autotuner may override it per step): steps with a small
+// side of at most 16 rows are bandwidth-bound and stay on the CUDA cores.
+inline bool skinny(int nM, int nN, int nK) {
+  (void)nK;
+  const int s = nM < nN ? nM : nN;
+  return s <= 4;
+}
+
+// Whether the rows kernel can run the step (small side <= 32 rows).
+inline bool rows_capable(int nM, int nN) { return (nM < nN ? nM : nN) <= 5; }
 
 // Tiny outputs (M, N <= 8) with a long contracted dimension: the dot kernel.
 inline bool use_dot(int nM, int nN, int nK) { return nM <= 3 && nN <= 3 && nK >= 10; }

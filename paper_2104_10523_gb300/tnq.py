@@ -39,7 +39,7 @@ EXPORTS = (
     "tnq_step_feature_count", "tnq_cost_model_create", "tnq_cost_model_destroy", "tnq_cost_model_workspace_bytes",
     "tnq_cost_model_n_params", "tnq_cost_model_bind", "tnq_cost_model_set_params", "tnq_cost_model_get_params",
     "tnq_cost_model_gradients", "tnq_cost_model_train", "tnq_cost_model_predict", "tnq_plan_step_features",
-    "tnq_plan_create_learned", "tnq_plan_get_candidates",
+    "tnq_plan_create_learned", "tnq_plan_get_candidates", "tnq_plan_autotune",
 )
 
 
@@ -124,6 +124,7 @@ def load() -> C.CDLL:
         "tnq_plan_step_features": ([vp, i32, fp], i32),
         "tnq_plan_create_learned": ([vp, vp, vp, C.POINTER(TnqPlanOpts), C.POINTER(vp)], i32),
         "tnq_plan_get_candidates": ([vp, dp, dp, i32, ip, ip, ip], i32),
+        "tnq_plan_autotune": ([vp, vp, i32, ip, ip], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -253,6 +254,13 @@ def tnq_contract_pair_noalloc(ctx, A, a_labels, B, b_labels, Cout, c_labels):
     check(load().tnq_contract_pair_noalloc(ctx, _ptr(A), len(a_labels), _int_array(a_labels), _ptr(B),
                                            len(b_labels), _int_array(b_labels), _ptr(Cout), len(c_labels),
                                            _int_array(c_labels)))
+
+
+def tnq_plan_autotune(ctx, plan, reps=3):
+    """Returns (steps on tensor cores, steps on CUDA cores) among the tuned steps."""
+    a, b = C.c_int(), C.c_int()
+    check(load().tnq_plan_autotune(ctx, plan, int(reps), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def tnq_ctx_set_graphs(ctx, enable: bool):

@@ -113,6 +113,22 @@ def test_graph_replay_identical_to_direct_launches(T, prec):
     assert rel_l2(g1, sv.amplitudes(c, bits)) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_autotuned_plan_parity(T, prec):
+    c = grid_circuit(4, 5, 10, 2021)
+    bits = random_bitstrings(20, 64, 5)
+    ref = sv.amplitudes(c, bits)
+    ctx = T.Context(0, prec)
+    plan = T.Plan(T.Circuit(c), batch_log2=6, path_mode=2, n_candidates=64, seed=3)
+    ctx.bind(plan)
+    before = ctx.amplitudes(plan, bits)
+    n_tc, n_cc = T.tnq_plan_autotune(ctx.h, plan.h, 2)
+    assert n_tc + n_cc >= 1
+    after = ctx.amplitudes(plan, bits)          # graph re-captured with the tuned choices
+    assert rel_l2(before, ref) <= TOL[prec]
+    assert rel_l2(after, ref) <= TOL[prec]
+
+
 def test_bad_bits_rejected(T, small_ref):
     c, _ = small_ref
     ctx = T.Context(0, "fp32")
