@@ -163,6 +163,15 @@ tnq_status tnq_plan_bind(tnq_ctx* ctx, tnq_plan* p, void* workspace, size_t byte
 tnq_status tnq_amplitudes(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t* bits,
                           double* out);
 
+/* Partial amplitudes: as tnq_amplitudes, but only slices slice_begin ..
+ * slice_begin + slice_count - 1 (of the plan's 2^n_sliced) are summed.  The
+ * slices of Sec. 3.1 are independent sub-networks, so summing the partial
+ * results of a partition of [0, 2^n_sliced) (in FP64, e.g. one block per GPU
+ * followed by one all-reduce) gives the amplitudes.  Errors: INVALID_ARG for a
+ * range outside [0, 2^n_sliced), otherwise as tnq_amplitudes. */
+tnq_status tnq_amplitudes_slices(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t* bits,
+                                 int64_t slice_begin, int64_t slice_count, double* out);
+
 /* Noisy probabilities p(x) = <x|rho|x> estimated from n_traj stochastic
  * trajectories (Eq. kraus_sum channels, one Kraus operator drawn per channel
  * with probability Tr(A_k^dagger A_k)/d and rescaled by its inverse square

@@ -242,6 +242,12 @@ tnq_status tnq_amplitudes(tnq_ctx* c, tnq_plan* p, int64_t n_bs, const int8_t* b
   return exec_amplitudes(&c->c, &p->p, n_bs, bits, out);
 }
 
+tnq_status tnq_amplitudes_slices(tnq_ctx* c, tnq_plan* p, int64_t n_bs, const int8_t* bits, int64_t slice_begin,
+                                 int64_t slice_count, double* out) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return exec_amplitudes_range(&c->c, &p->p, n_bs, bits, slice_begin, slice_count, out);
+}
+
 tnq_status tnq_noisy_probabilities(tnq_ctx* c, tnq_plan* p, int64_t n_traj, uint64_t seed, int64_t n_bs,
                                    const int8_t* bits, double* p_out, double* se_out) {
   if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");

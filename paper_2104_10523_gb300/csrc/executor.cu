@@ -441,6 +441,11 @@ tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes) {
 }
 
 tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, double* out) {
+  return exec_amplitudes_range(ctx, p, n_bs, bits, 0, int64_t(1) << p->slice_labels.size(), out);
+}
+
+tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, int64_t slice_begin,
+                                 int64_t slice_count, double* out) {
   if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
   if (p->net.noisy) return fail(TNQ_ERR_INVALID_ARG, "plan is for a noisy circuit; use tnq_noisy_probabilities");
   if (n_bs < 0 || (n_bs > 0 && (!bits || !out))) return fail(TNQ_ERR_INVALID_ARG, "bad bitstring/output buffers");
@@ -470,8 +475,11 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
     pos[j] = int(std::find(rl.begin(), rl.end(), p->net.batch_labels[j]) - rl.begin());
   TNQ_CUDA(cudaMemsetAsync(err_flag, 0, 2 * sizeof(int), ctx->stream));
   const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
-  const int n_slices = 1 << p->slice_labels.size();
-  const bool graphs = ctx->use_graphs && !ctx->timing;
+  const int64_t n_slices = int64_t(1) << p->slice_labels.size();
+  if (slice_begin < 0 || slice_count < 0 || slice_begin + slice_count > n_slices)
+    return fail(TNQ_ERR_INVALID_ARG, "slice range outside [0, 2^n_sliced)");
+  // the captured graph covers every slice; partial ranges launch directly
+  const bool graphs = ctx->use_graphs && !ctx->timing && slice_begin == 0 && slice_count == n_slices;
   for (int64_t base = 0; base < n_bs; base += per) {
     int64_t nv = std::min<int64_t>(per, n_bs - base);
     if (graphs && nv == per) {
@@ -496,8 +504,8 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
     TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w, bsrc, nv, err_flag, ctx->stream));
     ctx->launches++;
     TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
-    for (int s = 0; s < n_slices; ++s) {
-      tnq_status st = run_pass(ctx, p, s, ws);
+    for (int64_t s = slice_begin; s < slice_begin + slice_count; ++s) {
+      tnq_status st = run_pass(ctx, p, int(s), ws);
       if (st != TNQ_OK) return st;
     }
     double* dst = out_dev ? out + 2 * base : out_stage;

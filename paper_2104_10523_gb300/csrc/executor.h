@@ -44,6 +44,8 @@ tnq_status timing_collect(Ctx* ctx);  // after a stream sync
 
 tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes);
 tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, double* out);
+tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, int64_t slice_begin,
+                                 int64_t slice_count, double* out);
 tnq_status exec_noisy(Ctx* ctx, Plan* p, int64_t n_traj, uint64_t seed, int64_t n_bs, const int8_t* bits,
                       double* p_out, double* se_out);
 tnq_status exec_traj_amplitudes(Ctx* ctx, Plan* p, uint64_t seed, int64_t traj_begin, int64_t n_traj, int64_t n_bs,

@@ -39,7 +39,7 @@ EXPORTS = (
     "tnq_step_feature_count", "tnq_cost_model_create", "tnq_cost_model_destroy", "tnq_cost_model_workspace_bytes",
     "tnq_cost_model_n_params", "tnq_cost_model_bind", "tnq_cost_model_set_params", "tnq_cost_model_get_params",
     "tnq_cost_model_gradients", "tnq_cost_model_train", "tnq_cost_model_predict", "tnq_plan_step_features",
-    "tnq_plan_create_learned", "tnq_plan_get_candidates", "tnq_plan_autotune",
+    "tnq_plan_create_learned", "tnq_plan_get_candidates", "tnq_plan_autotune", "tnq_amplitudes_slices",
 )
 
 
@@ -125,6 +125,7 @@ def load() -> C.CDLL:
         "tnq_plan_create_learned": ([vp, vp, vp, C.POINTER(TnqPlanOpts), C.POINTER(vp)], i32),
         "tnq_plan_get_candidates": ([vp, dp, dp, i32, ip, ip, ip], i32),
         "tnq_plan_autotune": ([vp, vp, i32, ip, ip], i32),
+        "tnq_amplitudes_slices": ([vp, vp, i64, vp, i64, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -226,6 +227,11 @@ def tnq_amplitudes(ctx, plan, bits, out):
     """bits: int8 [n_bs][n] (NumPy host or torch device); out: float64 [n_bs][2] (same choices)."""
     n_bs = int(bits.shape[0])
     check(load().tnq_amplitudes(ctx, plan, n_bs, _ptr(bits), _ptr(out)))
+
+
+def tnq_amplitudes_slices(ctx, plan, bits, slice_begin, slice_count, out):
+    check(load().tnq_amplitudes_slices(ctx, plan, int(bits.shape[0]), _ptr(bits), int(slice_begin),
+                                       int(slice_count), _ptr(out)))
 
 
 def tnq_noisy_probabilities(ctx, plan, n_traj, seed, bits, p_out, se_out=None):

@@ -129,6 +129,32 @@ def test_autotuned_plan_parity(T, prec):
     assert rel_l2(after, ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("world", [2, 3])
+def test_slice_blocks_sum_to_amplitudes(T, small_ref, world):
+    """The per-rank partial amplitudes of a slice partition add up to the full
+    result (the ranks run one after the other on this GPU)."""
+    from paper_2104_10523_gb300 import parallel
+    c, ref = small_ref
+    ctx = T.Context(0, "fp32")
+    plan = T.Plan(T.Circuit(c), batch_log2=3, max_intermediate_log2=7, path_mode=0)
+    ctx.bind(plan)
+    n_slices = 2 ** plan.info["n_sliced"]
+    assert n_slices >= 4
+    bits = CONFIG_SMALL_BITS[:16]
+    full = ctx.amplitudes(plan, bits)
+    total = np.zeros((16, 2))
+    for r in range(world):
+        b, cnt = parallel.block_range(r, world, n_slices)
+        part = np.zeros((16, 2))
+        T.tnq_amplitudes_slices(ctx.h, plan.h, bits, b, cnt, part)
+        total += part
+    got = total[:, 0] + 1j * total[:, 1]
+    assert np.allclose(got, full, rtol=1e-12, atol=1e-15)
+    assert rel_l2(got, ref[:16]) <= TOL["fp32"]
+    with pytest.raises(T.TnqError):
+        T.tnq_amplitudes_slices(ctx.h, plan.h, bits, n_slices - 1, 2, part)
+
+
 def test_bad_bits_rejected(T, small_ref):
     c, _ = small_ref
     ctx = T.Context(0, "fp32")
