@@ -160,28 +160,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Launch order: within each (split, batch) the output tiles go in groups of
-  // TC_GROUP_M m-tiles with the n-tiles swept inside a group, so the CTAs of one
-  // wave share a few A' tile rows and B tiles in L2.
-  long long bid = blockIdx.x;
   const long long tiles = (long long)P.tiles_m * P.tiles_n;
-  const int pid = int(bid % tiles);
-  bid /= tiles;
-  const int split = int(bid % P.splits);
-  const int h = int(bid / P.splits);
-  const int per_group = TC_GROUP_M * P.tiles_n;
-  const int first_m = (pid / per_group) * TC_GROUP_M;
-  const int group_m = min(P.tiles_m - first_m, TC_GROUP_M);
-  const int mt = first_m + (pid % per_group) % group_m;
-  const int nt = (pid % per_group) / group_m;
-  const int kb_begin = split * P.kb_per_split;
-  const int nkb = min(P.nkb - kb_begin, P.kb_per_split);  // K blocks of this CTA (>= 1)
+  const long long total_tiles = tiles * P.splits * P.batch;
   const uint32_t stage_bytes = (P.split ? 2u : 1u) * (P.a_bytes + P.b_bytes);
-  const int nchunks = (nkb + P.chunk_kb - 1) / P.chunk_kb;
-  // one accumulator buffer when there is one chunk, else two (ping-pong)
   const uint32_t buf_cols = uint32_t(P.BN);
-  uint32_t tmem_cols = nchunks > 1 ? 2 * buf_cols : buf_cols;
-  if (tmem_cols < 32) tmem_cols = 32;
+  const uint32_t tmem_cols = 2 * buf_cols < 32 ? 32u : 2 * buf_cols;  // two accumulator buffers
+
+  // Tile t -> (m-tile, n-tile, split, batch).  Within each (split, batch) the
+  // output tiles go in groups of TC_GROUP_M m-tiles with the n-tiles swept
+  // inside a group, so the CTAs of one wave share A' tile rows and B tiles in L2.
+  auto decode = [&](long long t, int* mt, int* nt, int* split, int* h, int* kb0, int* nkb) {
+    const int pid = int(t % tiles);
+    long long r = t / tiles;
+    *split = int(r % P.splits);
+    *h = int(r / P.splits);
+    const int per_group = TC_GROUP_M * P.tiles_n;
+    const int first_m = (pid / per_group) * TC_GROUP_M;
+    const int group_m = min(P.tiles_m - first_m, TC_GROUP_M);
+    *mt = first_m + (pid % per_group) % group_m;
+    *nt = (pid % per_group) / group_m;
+    *kb0 = *split * P.kb_per_split;
+    *nkb = min(P.nkb - *kb0, P.kb_per_split);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) {
@@ -208,69 +208,100 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer: one ring of stages across all tiles of this CTA
     const int k_elems = P.kind_bf16 ? 64 : 32;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % P.stages;
-      const uint32_t ph = (kb / P.stages) & 1;
-      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
-        atomicOr(P.err, 1);
-        break;
-      }
-      uint8_t* st = smem + size_t(s) * stage_bytes;
-      const uint32_t fb = smem_u32(&full_bar[s]);
-      mbar_expect_tx(fb, stage_bytes);
-      const int kc = (kb_begin + kb) * k_elems;
-      uint8_t* a_hi = st;
-      uint8_t* b_hi = st + P.a_bytes;
-      tma_load_3d(smem_u32(a_hi), &ta_hi, kc, mt * TC_BM, h, fb);
-      tma_load_3d(smem_u32(b_hi), &tb_hi, kc, nt * P.BN, h, fb);
-      if (P.split) {
-        uint8_t* a_lo = st + P.a_bytes + P.b_bytes;
-        uint8_t* b_lo = a_lo + P.a_bytes;
-        tma_load_3d(smem_u32(a_lo), &ta_lo, kc, mt * TC_BM, h, fb);
-        tma_load_3d(smem_u32(b_lo), &tb_lo, kc, nt * P.BN, h, fb);
+    int s = 0;          // ring position and its phase, advanced per K block
+    uint32_t ph = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+      int mt, nt, split, h, kb0, nkb;
+      decode(t, &mt, &nt, &split, &h, &kb0, &nkb);
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
+          atomicOr(P.err, 1);
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + size_t(s) * stage_bytes;
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        mbar_expect_tx(fb, stage_bytes);
+        const int kc = (kb0 + kb) * k_elems;
+        tma_load_3d(smem_u32(st), &ta_hi, kc, mt * TC_BM, h, fb);
+        tma_load_3d(smem_u32(st + P.a_bytes), &tb_hi, kc, nt * P.BN, h, fb);
+        if (P.split) {
+          uint8_t* a_lo = st + P.a_bytes + P.b_bytes;
+          tma_load_3d(smem_u32(a_lo), &ta_lo, kc, mt * TC_BM, h, fb);
+          tma_load_3d(smem_u32(a_lo + P.a_bytes), &tb_lo, kc, nt * P.BN, h, fb);
+        }
+        if (++s == P.stages) {
+          s = 0;
+          ph ^= 1;
+        }
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % P.stages;
-      const uint32_t ph = (kb / P.stages) & 1;
-      const int c = kb / P.chunk_kb;
-      const int b = c & 1;
-      const bool chunk_start = (kb % P.chunk_kb) == 0;
-      if (chunk_start && c >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), ((c >> 1) - 1) & 1)) {
-        atomicOr(P.err, 1);
-        break;
-      }
-      if (!mbar_wait(smem_u32(&full_bar[s]), ph)) {
-        atomicOr(P.err, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint8_t* st = smem + size_t(s) * stage_bytes;
-      const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + P.a_bytes);
-      const uint32_t a_lo = smem_u32(st + P.a_bytes + P.b_bytes), b_lo = a_lo + P.a_bytes;
-      const uint32_t d = tmem + uint32_t(b) * buf_cols;
+    // ---------------- MMA issuer: accumulation chunks alternate between the two
+    // TMEM buffers across chunk and tile boundaries
+    int s = 0, b = 0;           // ring position / accumulator buffer
+    uint32_t ph = 0;            // ring phase
+    int uses[2] = {0, 0};       // chunks issued so far on each accumulator buffer
+    int chunk = 0, kc = 0;      // chunks issued; K blocks into the current chunk
+    bool ok = true;
+    for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+      int mt, nt, split, h, kb0, nkb;
+      decode(t, &mt, &nt, &split, &h, &kb0, &nkb);
+      kc = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const bool chunk_start = kc == 0;
+        if (chunk_start) {
+          b = chunk & 1;
+          // use u >= 1 of buffer b waits for the epilogue's drain of use u - 1,
+          // the (u-1)-th completion of acc_empty[b]
+          if (uses[b] >= 1 && !mbar_wait(smem_u32(&acc_empty[b]), uint32_t(uses[b] - 1) & 1)) {
+            atomicOr(P.err, 1);
+            ok = false;
+            break;
+          }
+        }
+        if (!mbar_wait(smem_u32(&full_bar[s]), ph)) {
+          atomicOr(P.err, 1);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint8_t* st = smem + size_t(s) * stage_bytes;
+        const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + P.a_bytes);
+        const uint32_t a_lo = smem_u32(st + P.a_bytes + P.b_bytes), b_lo = a_lo + P.a_bytes;
+        const uint32_t d = tmem + uint32_t(b) * buf_cols;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t off = kk * 32;
-        const uint32_t first = (chunk_start && kk == 0) ? 0u : 1u;
-        if (P.split) {
-          mma_issue(P.kind_bf16, d, smem_desc(a_lo + off), smem_desc(b_hi + off), P.idesc, first);
-          mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_lo + off), P.idesc, 1u);
-          mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, 1u);
-        } else {
-          mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, first);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint32_t first = (chunk_start && kk == 0) ? 0u : 1u;
+          if (P.split) {
+            mma_issue(P.kind_bf16, d, smem_desc(a_lo + off), smem_desc(b_hi + off), P.idesc, first);
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_lo + off), P.idesc, 1u);
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, 1u);
+          } else {
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, first);
+          }
+        }
+        mma_commit(smem_u32(&empty_bar[s]));
+        if (++s == P.stages) {
+          s = 0;
+          ph ^= 1;
+        }
+        if (++kc == P.chunk_kb || kb == nkb - 1) {
+          mma_commit(smem_u32(&acc_full[b]));
+          ++uses[b];
+          ++chunk;
+          kc = 0;
         }
       }
-      mma_commit(smem_u32(&empty_bar[s]));
-      if ((kb % P.chunk_kb) == P.chunk_kb - 1 || kb == nkb - 1) mma_commit(smem_u32(&acc_full[b]));
     }
     mma_commit(smem_u32(&final_bar));
   } else if (warp >= 2) {
-    // ---------------- epilogue: TMEM -> registers -> global
+    // ---------------- epilogue: drain every chunk into FP32 registers (round to
+    // nearest), write each finished tile
     const int quarter = warp & 3;        // TMEM lanes 32*quarter .. +31 belong to this warp
     const int half = (warp - 2) >> 2;    // which half of the BN columns
     const int nq_all = P.BN / 32;        // 32-column groups in the tile
@@ -279,19 +310,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nq = min(nq_all - q0, nq_half);  // groups owned by this warp (0..4)
     const uint32_t lane_addr = uint32_t(quarter * 32) << 16;
     const int row = quarter * 32 + lane;
-    const int grow = mt * TC_BM + row;  // row of A' within the batch
-    const int m = grow >> 1;
     const bool odd = lane & 1;
-    const size_t cbase = (size_t(h) * P.M + m) * size_t(P.N);
-    float acc[128];
-#pragma unroll
-    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+    long long chunk = 0;
     bool ok = true;
-    if (nchunks > 1) {
-      // drain every chunk into round-to-nearest FP32 registers
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int b = c & 1;
-        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[b]), (c >> 1) & 1));
+    for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+      int mt, nt, split, h, kb0, nkb;
+      decode(t, &mt, &nt, &split, &h, &kb0, &nkb);
+      const int nchunks = (nkb + P.chunk_kb - 1) / P.chunk_kb;
+      const int grow = mt * TC_BM + row;  // row of A' within the batch
+      const int m = grow >> 1;
+      const size_t cbase = (size_t(h) * P.M + m) * size_t(P.N);
+      float acc[128];
+#pragma unroll
+      for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+      for (int c = 0; c < nchunks; ++c, ++chunk) {
+        const int b = int(chunk & 1);
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[b]), uint32_t(chunk >> 1) & 1));
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -308,31 +342,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
       }
-    } else {
-      ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[0]), 0));
-      if (ok) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    if (!ok) {
-      if (lane == 0) atomicOr(P.err, 1);
-    } else {
+      if (!ok) {
+        if (lane == 0) atomicOr(P.err, 1);
+        break;
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (q >= nq) break;
-        float v[32];
-        if (nchunks > 1) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = acc[q * 32 + j];
-        } else {
-          uint32_t u[32];
-          TC_LD32(tmem + lane_addr + uint32_t((q0 + q) * 32), u);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
-        }
         float re[16], im[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const float mine_lo = v[j], mine_hi = v[16 + j];
+          const float mine_lo = acc[q * 32 + j], mine_hi = acc[q * 32 + 16 + j];
           const float other = __shfl_xor_sync(0xffffffffu, odd ? mine_lo : mine_hi, 1);
           // even lane (re row) keeps columns 0..15, odd lane (im row) keeps 16..31
           re[j] = odd ? other : mine_lo;
@@ -349,10 +369,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 16; ++j)
               if (n0 + j < P.N) {
-                double2 t = P.acc[cbase + n0 + j];
-                t.x += double(re[j]);
-                t.y += double(im[j]);
-                P.acc[cbase + n0 + j] = t;
+                double2 tt = P.acc[cbase + n0 + j];
+                tt.x += double(re[j]);
+                tt.y += double(im[j]);
+                P.acc[cbase + n0 + j] = tt;
               }
           } else if (n0 + 16 <= P.N) {
             float4* dst = reinterpret_cast<float4*>(P.C + cbase + n0);
@@ -369,7 +389,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   __syncthreads();
   if (warp == 1) {
-    // all MMAs of this CTA have completed before the accumulator is released
+    // all MMAs of this CTA have completed before the accumulators are released
     if (!mbar_wait(smem_u32(&final_bar), 0) && lane == 0) atomicOr(P.err, 1);
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -436,7 +456,6 @@ bool tc_gemm_supported(int M, int N, int K, int precision) {
 }
 
 cudaError_t launch_cgemm_tc(const TcGemmArgs& g, int sm_count, cudaStream_t st) {
-  (void)sm_count;
   if (!tc_gemm_supported(g.M, g.N, g.K, g.precision) || !g.err) return cudaErrorNotSupported;
   const bool bf16 = g.precision == TNQ_PREC_BF16X3;
   const bool split = g.precision != TNQ_PREC_TF32;
@@ -460,7 +479,7 @@ cudaError_t launch_cgemm_tc(const TcGemmArgs& g, int sm_count, cudaStream_t st) 
   P.stages = std::min<int>(TC_MAX_STAGES, TC_SMEM_BUDGET / int(stage_bytes));
   if (P.stages < 2) return cudaErrorNotSupported;
   P.stage_tx = stage_bytes;
-  P.chunk_kb = split ? 2 : P.nkb;
+  P.chunk_kb = split ? 2 : (1 << 30);  // non-split modes: one chunk per tile
   // instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1), K-major, N >> 3, M >> 4
   const uint32_t fmt = bf16 ? 1u : 2u;
   P.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(TC_BM >> 4) << 24);
@@ -488,7 +507,11 @@ cudaError_t launch_cgemm_tc(const TcGemmArgs& g, int sm_count, cudaStream_t st) 
   const int smem = int(P.stages * stage_bytes) + 1024;
   cudaError_t pe = tc_gemm_prepare();
   if (pe != cudaSuccess) return pe;
-  cgemm_tc_kernel<<<unsigned(total), TC_THREADS, smem, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, P);
+  // Short-K tiles: persistent CTAs (one per SM) loop over their tiles so the
+  // next tile's loads and MMAs overlap this tile's epilogue.  Long-K tiles:
+  // one CTA per tile (the loop runs once), which measured faster there.
+  const long long grid = P.kb_per_split <= 16 ? std::min<long long>(total, std::max(1, sm_count)) : total;
+  cgemm_tc_kernel<<<unsigned(grid), TC_THREADS, smem, st>>>(ma_hi, ma_lo, mb_hi, mb_lo, P);
   if (g.splits_used) *g.splits_used = P.splits;
   return cudaGetLastError();
 }
