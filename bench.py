@@ -325,7 +325,7 @@ def roofline_of(rec, precision):
         src = "fallback"
     if len(rec) == 0:
         return None, None
-    kinds = {0: "permute", 1: "cgemm_simt", 2: "cgemm_tc", 3: "other", 4: "cgemm_skinny"}
+    kinds = {0: "permute", 1: "cgemm_simt", 2: "cgemm_tc", 3: "other", 4: "cgemm_skinny", 5: "cgemm_tc_rows"}
     tot = {}
     for r in rec:
         k = int(r[0])
@@ -423,7 +423,7 @@ def run_pair(a, local, rank):
     step()
     rec = tnq.tnq_ctx_get_timings(ctx.h)
     roofline, share = roofline_of(rec, a.precision)
-    rows = np.random.default_rng(1).choice(2 ** m, size=16, replace=False)
+    rows = np.random.default_rng(1).choice(2 ** m, size=min(16, 2 ** m), replace=False)
     ref = contraction.sampled_rows(A, al, B, bl, ol, rows, ol[:m])
     got = C.cpu().numpy().reshape(2 ** n, 2 ** m).T[rows]
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))

@@ -132,12 +132,18 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
   StepOperands op;
   PermDesc d;
   const int ns = (int)slice_labels.size();
-  if (!use_tc && (rows_capable(nM, nN) || use_dot(nM, nN, nK)) && part) {
+  // Tall-skinny steps in the tensor-core modes: the large operand is gathered,
+  // split and multiplied on the tensor cores in one kernel (choice 2, and the
+  // default where the shape qualifies).
+  const int n_small = std::min(nM, nN), n_big = std::max(nM, nN);
+  const bool tc_rows_ok = choice != 0 && choice != 1 && tc_ok && rows_capable(nM, nN) && !use_dot(nM, nN, nK) &&
+                          tc_rows_supported(1 << n_small, 1 << n_big, 1 << nK, 1 << nH, n_big + nH, ctx->precision);
+  if (tc_rows_ok || (!use_tc && (rows_capable(nM, nN) || use_dot(nM, nN, nK)) && part)) {
     // bandwidth-bound skinny step: complex64 operands in [h][m|n][k] order
     // The large operand of a short-K rows step is read in place (fused gather)
     // instead of being permuted first.
     const bool small_is_a = nM <= nN;
-    const bool gather = !use_dot(nM, nN, nK) && nK <= 5 && (small_is_a ? perm_b : perm_a);
+    const bool gather = tc_rows_ok || (!use_dot(nM, nN, nK) && nK <= 5 && (small_is_a ? perm_b : perm_a));
     if (perm_a && !(gather && !small_is_a)) {
       build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(),
                       ns, PM_C64, nK, &d);
@@ -169,10 +175,17 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
                      8.0 * (std::ldexp(1.0, nH + nM + nK) + std::ldexp(1.0, nH + nN + nK) +
                             (acc ? 2.0 : 1.0) * std::ldexp(1.0, nH + nM + nN)),
                      0.f};
+      if (tc_rows_ok) r.kind = 5;
       int slot = timing_begin(ctx);
-      cudaError_t e = small_is_a
-                          ? launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, M, N, K, H, N, 1, slice_id, ctx->stream)
-                          : launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, N, M, K, H, 1, N, slice_id, ctx->stream);
+      cudaError_t e;
+      if (tc_rows_ok)
+        e = small_is_a ? launch_cgemm_tc_rows(Ssm, Gs, gd, C, acc, M, N, K, H, N, 1, slice_id, ctx->precision, err,
+                                              ctx->sm_count, ctx->stream)
+                       : launch_cgemm_tc_rows(Ssm, Gs, gd, C, acc, N, M, K, H, 1, N, slice_id, ctx->precision, err,
+                                              ctx->sm_count, ctx->stream);
+      else
+        e = small_is_a ? launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, M, N, K, H, N, 1, slice_id, ctx->stream)
+                       : launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, N, M, K, H, 1, N, slice_id, ctx->stream);
       timing_end(ctx, slot, r);
       TNQ_CUDA(e);
       ctx->launches++;
@@ -546,9 +559,14 @@ tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda) {
                        tc_gemm_supported(1 << s.nM, 1 << s.nN, 1 << s.nK, ctx->precision) &&
                        s.nM + s.nN + s.nK + s.nH >= 12;
     if (!tc_ok) continue;  // one candidate only
+    // candidates: 0 CUDA cores, 1 tensor-core GEMM, 2 tall-skinny tensor-core kernel
+    const int n_small = std::min(s.nM, s.nN), n_big = std::max(s.nM, s.nN);
+    const bool rows_ok = rows_capable(s.nM, s.nN) && !use_dot(s.nM, s.nN, s.nK) &&
+                         tc_rows_supported(1 << n_small, 1 << n_big, 1 << s.nK, 1 << s.nH, n_big + s.nH,
+                                           ctx->precision);
     float best = 0;
     int pick = -1;
-    for (int c = 0; c < 2 && result == TNQ_OK; ++c) {
+    for (int c = 0; c < (rows_ok ? 3 : 2) && result == TNQ_OK; ++c) {
       float tmin = 1e30f;
       for (int r = 0; r < reps + 1; ++r) {  // first run warms up
         cudaEventRecord(e0, ctx->stream);
@@ -570,7 +588,7 @@ tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda) {
       }
     }
     choice[si] = (int8_t)pick;
-    (pick == 1 ? ntc : ncc)++;
+    (pick >= 1 ? ntc : ncc)++;
   }
   ctx->timing = timing;
   cudaEventDestroy(e0);

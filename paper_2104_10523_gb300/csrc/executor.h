@@ -10,7 +10,8 @@ namespace tnq {
 
 // One kernel launch as seen by the optional timing recorder.
 struct KernelRecord {
-  int kind;        // 0 permute, 1 SIMT GEMM, 2 tensor-core GEMM, 3 other, 4 skinny (rows/dot) GEMM
+  int kind;        // 0 permute, 1 SIMT GEMM, 2 tensor-core GEMM, 3 other, 4 skinny (rows/dot) GEMM,
+                   // 5 tall-skinny tensor-core GEMM
   int step;        // plan step index (-1 outside a plan)
   int nH, nM, nN, nK;
   double flops;    // algorithmic flops (8 per complex multiply-add)

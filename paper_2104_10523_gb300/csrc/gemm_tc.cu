@@ -33,17 +33,19 @@
 #include <mutex>
 
 #include "gemm_tc.cuh"
+#include "tc_ptx.cuh"
 #include "../../include/tnq.h"
 
 namespace tnq {
 
 namespace {
 
+using namespace tcx;
+
 constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int TC_BM = 128;            // rows of A' per tile (64 complex rows)
 constexpr int TC_ROW_BYTES = 128;     // one 128B swizzle atom of K per stage
 constexpr int TC_MAX_STAGES = 8;
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 constexpr int TC_SMEM_BUDGET = 200 * 1024;
 constexpr int TC_GROUP_M = 16;         // m-tiles per launch-order group
 
@@ -68,83 +70,6 @@ struct TcParams {
   double2* acc;
   int* err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-
-// Bounded wait for the phase of parity `parity` to complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-      "[%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand in 128B-swizzled rows,
-// 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= uint64_t((saddr & 0x3FFFF) >> 4);
-  d |= uint64_t(16 >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
-  d |= uint64_t(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
-  d |= uint64_t(1) << 46;           // descriptor version for sm_100 family
-  d |= uint64_t(2) << 61;           // 128-byte swizzle
-  return d;
-}
-
-__device__ __forceinline__ void mma_issue(int kind_bf16, uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                          uint32_t accumulate) {
-  if (kind_bf16) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
-  } else {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-#define TC_LD32(taddr, v)                                                                                      \
-  asm volatile(                                                                                                \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18," \
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                           \
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),       \
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),  \
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), \
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])  \
-      : "r"(taddr))
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
@@ -443,6 +368,7 @@ cudaError_t tc_gemm_prepare() {
     result = encode_fn() ? cudaSuccess : cudaErrorNotSupported;
     if (result == cudaSuccess)
       result = cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BUDGET + 1024);
+    if (result == cudaSuccess) result = tc_rows_prepare();
   });
   return result;
 }

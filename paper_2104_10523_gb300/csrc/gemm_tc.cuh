@@ -32,4 +32,17 @@ bool tc_gemm_supported(int M, int N, int K, int precision);
 // Returns cudaErrorNotSupported when the shape cannot run on the tensor cores.
 cudaError_t launch_cgemm_tc(const TcGemmArgs& g, int sm_count, cudaStream_t st);
 
+struct GatherDesc;
+
+// Tall-skinny tensor-core GEMM (gemm_tc_rows.cu): out[h][s][g] (strides
+// s_stride_out, g_stride_out; batch stride ns * ng) = sum_k S[h][s][k] G[h][g][k]
+// for a small operand S ([batch][ns][K] complex64) and a large one G read in
+// its stored bit order through gd, split into BF16 or TF32 hi/lo parts in
+// shared memory.  Adds into the FP64 acc when non-null, else writes C.
+bool tc_rows_supported(int ns, int ng, int K, int batch, int nrow, int precision);
+cudaError_t tc_rows_prepare();
+cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
+                                 int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
+                                 int precision, int* err, int sm_count, cudaStream_t st);
+
 }  // namespace tnq

@@ -1,0 +1,458 @@
+// Tall-skinny complex GEMM on the tcgen05 tensor cores, sm_103a.
+//
+// Steps of the contraction sequence (Sec. 3.1) whose one operand is small
+// (ns <= 32 rows) and whose contracted extent is short (K <= 32) but whose
+// other operand G is large (ng rows, up to 2^24 and more) do 8 * ns real flops
+// per byte of G: too few for a tensor-core tile built the ordinary way (the
+// 2 * ns-row expansion of the small operand would fill a quarter of a 128-row
+// MMA), too many for the CUDA cores to keep up with HBM.  Here the roles are
+// swapped: 128 rows of G form the MMA's M side, the expanded small operand
+//   S' (2 ns x 2K):  row (s, re) = [sr_0, -si_0, sr_1, -si_1, ...]
+//                    row (s, im) = [si_0,  sr_0, si_1,  sr_1, ...]
+// its N side, and D = G * S'^T leaves Re/Im of out[s][g] in TMEM columns
+// (2s, 2s+1) of lane g.
+//
+// G is read once from HBM, in its stored bit order (the gather of the permute
+// is fused: the row and K bits of G sit at arbitrary positions of the stored
+// tensor), split into hi/lo parts (BF16 or TF32) by converter warps and written
+// straight into the 128-byte-swizzled K-major layout the MMA reads.  The
+// output is written once.  Per 128-row tile: 128 * K * 8 bytes in, 128 * ns * 8
+// bytes out, 3 * ceil(2K / k_step) MMAs of 128 x Npad (Npad = max(16, 2 ns)).
+//
+// CTA (persistent, one per SM) = 13 warps:
+//   warps 0-7   converters, two groups of four; group g fills the stages of
+//               the CTA's tiles i = g, g + 2, ...: each thread owns one tile
+//               row, loads it (16-byte pairs when the lowest stored bit is a
+//               K bit), splits it, stores it swizzled, and prefetches its row
+//               of the group's next tile before waiting for a free stage;
+//   warp 8      allocates TMEM and (one thread) issues the MMAs of each tile
+//               into one of NACC accumulator buffers;
+//   warps 9-12  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and writes
+//               complex64 outputs (or adds into the FP64 cross-slice sum).
+// Every mbarrier wait is bounded; one that runs out sets the error flag and
+// the CTA unwinds.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "gemm_tc.cuh"
+#include "kernels.cuh"
+#include "tc_ptx.cuh"
+#include "../../include/tnq.h"
+
+namespace tnq {
+
+namespace {
+
+using namespace tcx;
+
+constexpr int TR_CONV_WARPS = 8;
+constexpr int TR_THREADS = 32 * (TR_CONV_WARPS + 1 + 4);
+constexpr int TR_MMA_WARP = TR_CONV_WARPS;
+constexpr int TR_STAGES = 4;      // even: stage parity = converter group
+constexpr int TR_NACC = 4;        // TMEM accumulator buffers
+constexpr int TR_ROW_BYTES = 128; // one swizzle atom per tile row (all of K)
+constexpr int TR_STAGE_BYTES = 2 * 128 * TR_ROW_BYTES;  // hi + lo
+constexpr int TR_BPRIME_BUDGET = 64 * 1024;
+
+struct TrParams {
+  const float2* S;        // small operand [batch][ns][K]
+  const float2* G;        // large operand, stored bit order (see gd)
+  GatherDesc gd;          // rows: g bits then batch bits; K bits in contraction order
+  int ns, ng, K, batch;
+  int npad;               // MMA N: max(16, 2 ns)
+  int nks;                // MMA K steps (32 bytes of K per step)
+  int kind_bf16;          // 1: BF16 parts, kind::f16; 0: TF32 parts, kind::tf32
+  int split;              // 1: three products (hi/lo); 0: one TF32 product
+  int pairs;              // the lowest stored bit of G is K bit 0: 16-byte loads
+  long long s_stride, g_stride;
+  int tiles_per_h;        // ng / 128
+  long long total_tiles;
+  int slice_id;
+  uint32_t idesc;
+  float2* C;
+  double2* acc;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  return uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(x)));
+}
+
+__device__ __forceinline__ float bf16_val(uint32_t b) { return __uint_as_float(b << 16); }
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// hi/lo words of two reals (x0, x1) packed for one 4-byte slot of a BF16 row.
+__device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t* hi, uint32_t* lo) {
+  const uint32_t h0 = bf16_bits(x0), h1 = bf16_bits(x1);
+  const uint32_t l0 = bf16_bits(x0 - bf16_val(h0)), l1 = bf16_bits(x1 - bf16_val(h1));
+  *hi = h0 | (h1 << 16);
+  *lo = l0 | (l1 << 16);
+}
+
+// Byte offset of 16-byte chunk j of row r in a 128-byte-swizzled K-major tile
+// (8-row groups of 1024 bytes; chunk index XOR row-in-group).
+__device__ __forceinline__ uint32_t swz(int r, int j) { return uint32_t(r) * 128u + (uint32_t(j ^ (r & 7)) << 4); }
+
+// Split the 2K reals of one row (complex v[0..K-1], zero beyond K) and store the
+// first nks * 32 bytes of its hi and lo rows.
+template <int KMAX>
+__device__ __forceinline__ void store_row(uint8_t* hi, uint8_t* lo, int r, const float2 (&v)[KMAX], int nks,
+                                          int kind_bf16, int split) {
+  if (kind_bf16) {
+    // chunk j: complex 4j .. 4j+3 (8 BF16 reals); two chunks per 32-byte K step
+#pragma unroll
+    for (int j = 0; j < KMAX / 4; ++j) {
+      if (j < 2 * nks) {
+        uint4 h, l;
+        bf16_split2(v[4 * j].x, v[4 * j].y, &h.x, &l.x);
+        bf16_split2(v[4 * j + 1].x, v[4 * j + 1].y, &h.y, &l.y);
+        bf16_split2(v[4 * j + 2].x, v[4 * j + 2].y, &h.z, &l.z);
+        bf16_split2(v[4 * j + 3].x, v[4 * j + 3].y, &h.w, &l.w);
+        *reinterpret_cast<uint4*>(hi + swz(r, j)) = h;
+        *reinterpret_cast<uint4*>(lo + swz(r, j)) = l;
+      }
+    }
+  } else {
+    // chunk j: complex 2j, 2j+1 (4 TF32 reals); two chunks per 32-byte K step
+#pragma unroll
+    for (int j = 0; j < KMAX / 2; ++j) {
+      if (j < 2 * nks) {
+        float4 h, l;
+        h.x = tf32_rna(v[2 * j].x);
+        h.y = tf32_rna(v[2 * j].y);
+        h.z = tf32_rna(v[2 * j + 1].x);
+        h.w = tf32_rna(v[2 * j + 1].y);
+        *reinterpret_cast<float4*>(hi + swz(r, j)) = h;
+        if (split) {
+          l.x = tf32_rna(v[2 * j].x - h.x);
+          l.y = tf32_rna(v[2 * j].y - h.y);
+          l.z = tf32_rna(v[2 * j + 1].x - h.z);
+          l.w = tf32_rna(v[2 * j + 1].y - h.w);
+          *reinterpret_cast<float4*>(lo + swz(r, j)) = l;
+        }
+      }
+    }
+  }
+}
+
+// Expanded small operand S' for every batch entry: rows n < npad of 2K reals,
+// hi and lo, built by the converter threads at kernel start.
+__device__ void build_bprime(const TrParams& P, uint8_t* bp, int tid, int nthreads) {
+  const int es = P.kind_bf16 ? 2 : 4;
+  const int reals = P.nks * (32 / es);  // reals per row the MMAs read
+  const int per_h = P.npad * reals;
+  const uint32_t half_bytes = uint32_t(P.npad) * TR_ROW_BYTES;
+  for (int e = tid; e < P.batch * per_h; e += nthreads) {
+    const int h = e / per_h, rem = e % per_h, n = rem / reals, q = rem % reals;
+    const int s = n >> 1, k = q >> 1;
+    float x = 0.f;
+    if (s < P.ns && k < P.K) {
+      const float2 a = P.S[(size_t(h) * P.ns + s) * P.K + k];
+      // row (s, re): [sr, -si] per k; row (s, im): [si, sr]
+      x = (n & 1) ? ((q & 1) ? a.x : a.y) : ((q & 1) ? -a.y : a.x);
+    }
+    uint8_t* hi = bp + size_t(h) * 2 * half_bytes;
+    uint8_t* lo = hi + half_bytes;
+    const uint32_t off = swz(n, (q * es) >> 4) + uint32_t((q * es) & 15);
+    if (P.kind_bf16) {
+      const uint32_t hb = bf16_bits(x);
+      *reinterpret_cast<unsigned short*>(hi + off) = (unsigned short)hb;
+      *reinterpret_cast<unsigned short*>(lo + off) = (unsigned short)bf16_bits(x - bf16_val(hb));
+    } else {
+      const float hv = tf32_rna(x);
+      *reinterpret_cast<float*>(hi + off) = hv;
+      *reinterpret_cast<float*>(lo + off) = tf32_rna(x - hv);
+    }
+  }
+}
+
+// Row r of tile t: (batch entry, first row) and the stored offset of its K = 0
+// element, from the row bits' positions (bits 0-6 of the row index are r).
+struct RowAddr {
+  size_t lo;  // r's bits deposited at rowpos[0..6]
+};
+
+__device__ __forceinline__ size_t deposit(long long v, const int* pos, int n) {
+  size_t o = 0;
+  for (int j = 0; j < n; ++j)
+    if ((v >> j) & 1) o |= size_t(1) << pos[j];
+  return o;
+}
+
+template <int KMAX>
+__device__ __forceinline__ void load_row(const TrParams& P, const uint32_t* koff, size_t base, float2 (&v)[KMAX]) {
+  if (P.pairs) {
+#pragma unroll
+    for (int kk = 0; kk < KMAX; kk += 2) {
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kk < P.K) t = __ldg(reinterpret_cast<const float4*>(P.G + base + koff[kk]));
+      v[kk] = make_float2(t.x, t.y);
+      v[kk + 1] = make_float2(t.z, t.w);
+    }
+  } else {
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk) v[kk] = kk < P.K ? __ldg(P.G + base + koff[kk]) : make_float2(0.f, 0.f);
+  }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __grid_constant__ TrParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[TR_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[TR_STAGES];
+  __shared__ __align__(8) uint64_t acc_full[TR_NACC];
+  __shared__ __align__(8) uint64_t acc_empty[TR_NACC];
+  __shared__ __align__(8) uint64_t final_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint32_t koff[KMAX];
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* bprime = smem + TR_STAGES * TR_STAGE_BYTES;
+  const uint32_t bp_half = uint32_t(P.npad) * TR_ROW_BYTES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tmem_cols = uint32_t(P.npad * TR_NACC) < 32u ? 32u : uint32_t(P.npad * TR_NACC);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TR_STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 128);  // one converter group
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < TR_NACC; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(smem_u32(&final_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int kk = threadIdx.x; kk < KMAX; kk += blockDim.x) {
+    uint32_t o = 0;
+    for (int j = 0; j < P.gd.nk; ++j)
+      if ((kk >> j) & 1) o |= 1u << P.gd.kpos[j];
+    koff[kk] = o;
+  }
+  if (warp < TR_CONV_WARPS) build_bprime(P, bprime, threadIdx.x, 32 * TR_CONV_WARPS);
+  if (warp == TR_MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  // S' written by generic stores becomes visible to the MMA (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const long long stride = gridDim.x;
+
+  if (warp < TR_CONV_WARPS) {
+    // ---------------- converters: group grp fills the stages of tiles grp, grp+2, ...
+    const int grp = warp >> 2, r = (warp & 3) * 32 + lane;
+    const int nhi = P.gd.nrow - 7;
+    size_t soff = 0;
+    for (int j = 0; j < P.gd.n_slice; ++j)
+      if (P.gd.slice_src[j] >= 0 && ((P.slice_id >> j) & 1)) soff |= size_t(1) << P.gd.slice_src[j];
+    const size_t lo = soff | deposit(r, P.gd.rowpos, 7);
+    auto row_base = [&](long long t) {
+      const long long h = t / P.tiles_per_h, g0 = (t % P.tiles_per_h) * 128;
+      return lo | deposit((h * P.ng + g0) >> 7, P.gd.rowpos + 7, nhi);
+    };
+    float2 cur[KMAX], nxt[KMAX];
+    long long i = grp;
+    long long t = blockIdx.x + i * stride;
+    if (t < P.total_tiles) load_row<KMAX>(P, koff, row_base(t), cur);
+    for (; t < P.total_tiles; i += 2, t += 2 * stride) {
+      const long long tn = t + 2 * stride;
+      if (tn < P.total_tiles) load_row<KMAX>(P, koff, row_base(tn), nxt);
+      const int s = int(i % TR_STAGES);
+      const uint32_t use = uint32_t(i / TR_STAGES);
+      if (!mbar_wait(smem_u32(&empty_bar[s]), (use & 1) ^ 1)) {
+        atomicOr(P.err, 1);
+        break;
+      }
+      uint8_t* st = smem + size_t(s) * TR_STAGE_BYTES;
+      store_row<KMAX>(st, st + TR_STAGE_BYTES / 2, r, cur, P.nks, P.kind_bf16, P.split);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&full_bar[s]));
+#pragma unroll
+      for (int kk = 0; kk < KMAX; ++kk) cur[kk] = nxt[kk];
+    }
+  } else if (warp == TR_MMA_WARP) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      long long i = 0;
+      for (long long t = blockIdx.x; t < P.total_tiles; t += stride, ++i) {
+        const int s = int(i % TR_STAGES), b = int(i % TR_NACC);
+        if (i >= TR_NACC && !mbar_wait(smem_u32(&acc_empty[b]), uint32_t(i / TR_NACC - 1) & 1)) {
+          atomicOr(P.err, 1);
+          break;
+        }
+        if (!mbar_wait(smem_u32(&full_bar[s]), uint32_t(i / TR_STAGES) & 1)) {
+          atomicOr(P.err, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int h = int(t / P.tiles_per_h);
+        const uint32_t a_hi = smem_u32(smem + size_t(s) * TR_STAGE_BYTES), a_lo = a_hi + TR_STAGE_BYTES / 2;
+        const uint32_t b_hi = smem_u32(bprime) + uint32_t(h) * 2 * bp_half, b_lo = b_hi + bp_half;
+        const uint32_t d = tmem + uint32_t(b * P.npad);
+        for (int kk = 0; kk < P.nks; ++kk) {
+          const uint32_t off = kk * 32;
+          if (P.split) {
+            mma_issue(P.kind_bf16, d, smem_desc(a_lo + off), smem_desc(b_hi + off), P.idesc, kk > 0 ? 1u : 0u);
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_lo + off), P.idesc, 1u);
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, 1u);
+          } else {
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, kk > 0 ? 1u : 0u);
+          }
+        }
+        mma_commit(smem_u32(&empty_bar[s]));
+        mma_commit(smem_u32(&acc_full[b]));
+      }
+      mma_commit(smem_u32(&final_bar));
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue
+    const int quarter = warp & 3;
+    const uint32_t lane_addr = uint32_t(quarter * 32) << 16;
+    const int row = quarter * 32 + lane;
+    long long i = 0;
+    for (long long t = blockIdx.x; t < P.total_tiles; t += stride, ++i) {
+      const int b = int(i % TR_NACC);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[b]), uint32_t(i / TR_NACC) & 1));
+      if (!ok) {
+        if (lane == 0) atomicOr(P.err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[64];
+      const uint32_t base = tmem + lane_addr + uint32_t(b * P.npad);
+      TC_LD16(base, v);
+      if (P.npad > 16) TC_LD16(base + 16, (v + 16));
+      if (P.npad > 32) {
+        TC_LD16(base + 32, (v + 32));
+        TC_LD16(base + 48, (v + 48));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+      const long long h = t / P.tiles_per_h;
+      const long long g = (t % P.tiles_per_h) * 128 + row;
+      const size_t obase = size_t(h) * P.ns * P.ng + size_t(g) * P.g_stride;
+#pragma unroll
+      for (int s = 0; s < 32; ++s) {
+        if (s >= P.ns) break;
+        const float re = __uint_as_float(v[2 * s]), im = __uint_as_float(v[2 * s + 1]);
+        const size_t o = obase + size_t(s) * P.s_stride;
+        if (P.acc) {
+          double2 a = P.acc[o];
+          a.x += double(re);
+          a.y += double(im);
+          P.acc[o] = a;
+        } else {
+          P.C[o] = make_float2(re, im);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == TR_MMA_WARP) {
+    // every MMA of this CTA has completed before TMEM is released
+    if (!mbar_wait(smem_u32(&final_bar), 0) && lane == 0) atomicOr(P.err, 1);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+int tr_npad(int ns) { return std::max(16, (2 * ns + 15) / 16 * 16); }
+
+size_t tr_smem_bytes(int ns, int batch) {
+  return size_t(TR_STAGES) * TR_STAGE_BYTES + size_t(batch) * 2 * tr_npad(ns) * TR_ROW_BYTES + 1024;
+}
+
+constexpr size_t TR_SMEM_MAX = size_t(TR_STAGES) * TR_STAGE_BYTES + TR_BPRIME_BUDGET + 1024;
+
+}  // namespace
+
+cudaError_t tc_rows_prepare() {
+  static cudaError_t result = cudaErrorUnknown;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TR_SMEM_MAX));
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(TR_SMEM_MAX));
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(TR_SMEM_MAX));
+  });
+  return result;
+}
+
+bool tc_rows_supported(int ns, int ng, int K, int batch, int nrow, int precision) {
+  if (precision != TNQ_PREC_TF32 && precision != TNQ_PREC_TF32X3 && precision != TNQ_PREC_BF16X3) return false;
+  const int kmax = precision == TNQ_PREC_BF16X3 ? 32 : 16;  // 2K reals fit one 128-byte row
+  if (ns < 1 || ns > 32 || K < 1 || K > kmax || ng < 128 || (ng & 127) || batch < 1 || nrow < 7) return false;
+  return size_t(batch) * 2 * tr_npad(ns) * TR_ROW_BYTES <= size_t(TR_BPRIME_BUDGET);
+}
+
+cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
+                                 int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
+                                 int precision, int* err, int sm_count, cudaStream_t st) {
+  if (!tc_rows_supported(ns, ng, K, batch, gd.nrow, precision) || !err) return cudaErrorNotSupported;
+  if (gd.nk > 5 || gd.nrow > 32 || (1 << gd.nk) != K) return cudaErrorInvalidValue;
+  cudaError_t pe = tc_rows_prepare();
+  if (pe != cudaSuccess) return pe;
+  TrParams P;
+  P.S = reinterpret_cast<const float2*>(Ssmall);
+  P.G = reinterpret_cast<const float2*>(Gsrc);
+  P.gd = gd;
+  P.ns = ns;
+  P.ng = ng;
+  P.K = K;
+  P.batch = batch;
+  P.npad = tr_npad(ns);
+  P.kind_bf16 = precision == TNQ_PREC_BF16X3 ? 1 : 0;
+  P.split = precision == TNQ_PREC_TF32 ? 0 : 1;
+  const int k_step = P.kind_bf16 ? 8 : 4;  // complex values per 32-byte MMA K step
+  P.nks = (K + k_step - 1) / k_step;
+  P.pairs = gd.nk >= 1 && gd.kpos[0] == 0;
+  P.s_stride = s_stride_out;
+  P.g_stride = g_stride_out;
+  P.tiles_per_h = ng / 128;
+  P.total_tiles = (long long)P.tiles_per_h * batch;
+  P.slice_id = slice_id;
+  // instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1), K-major, N >> 3, M >> 4
+  const uint32_t fmt = P.kind_bf16 ? 1u : 2u;
+  P.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(P.npad >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+  P.C = reinterpret_cast<float2*>(C);
+  P.acc = reinterpret_cast<double2*>(acc);
+  P.err = err;
+  const long long grid = std::min<long long>(P.total_tiles, std::max(1, sm_count));
+  const size_t smem = tr_smem_bytes(ns, batch);
+  if (K <= 8)
+    cgemm_tc_rows_kernel<8><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+  else if (K <= 16)
+    cgemm_tc_rows_kernel<16><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+  else
+    cgemm_tc_rows_kernel<32><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace tnq

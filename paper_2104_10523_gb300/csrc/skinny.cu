@@ -98,88 +98,111 @@ __global__ void __launch_bounds__(RW_THREADS) cgemm_rows_kernel(
 
 constexpr int DOT_THREADS = 256;
 
-// MX x MX complex sums per thread (MX = 4 or 8): register accumulators over the
-// thread's part of K, then a fixed-order reduction over the CTA.
-template <int MX>
-__global__ void __launch_bounds__(DOT_THREADS) cdot_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                           float2* __restrict__ part, int M, int N, int K,
-                                                           int kchunk) {
-  __shared__ float red[DOT_THREADS / 32][2 * MX * MX];
+// Dot products for M, N <= 8: the M x N outputs form (M / TM) x (N / TN) <= 4
+// blocks of TM x TN (TM = min(M, 4), TN = min(N, 4)); the block index sits in
+// the low bits of the thread index, so the lanes of one warp that share a row
+// read it in the same 16-byte load instruction and every loaded value serves
+// TN (or TM) complex multiply-adds from registers.  Each thread keeps two
+// K-pairs in flight per iteration; per-CTA partials go to part[split][batch][M][N].
+template <int TM, int TN>
+__device__ __forceinline__ void cdot_load(const float2* __restrict__ Ar, const float2* __restrict__ Br, int K, int k,
+                                          int kend, float4 (&a)[TM], float4 (&b)[TN]) {
+  const bool in = k < kend, two = k + 1 < kend;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (two) a[i] = *reinterpret_cast<const float4*>(Ar + size_t(i) * K + k);
+    else if (in) { const float2 v = Ar[size_t(i) * K + k]; a[i].x = v.x; a[i].y = v.y; }
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    b[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (two) b[j] = *reinterpret_cast<const float4*>(Br + size_t(j) * K + k);
+    else if (in) { const float2 v = Br[size_t(j) * K + k]; b[j].x = v.x; b[j].y = v.y; }
+  }
+}
+
+template <int TM, int TN>
+__device__ __forceinline__ void cdot_fma(const float4 (&a)[TM], const float4 (&b)[TN], float (&cr)[TM][TN],
+                                         float (&ci)[TM][TN]) {
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
+      cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
+      ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
+      ci[i][j] = fmaf(a[i].y, b[j].x, ci[i][j]);
+      cr[i][j] = fmaf(a[i].z, b[j].z, cr[i][j]);
+      cr[i][j] = fmaf(-a[i].w, b[j].w, cr[i][j]);
+      ci[i][j] = fmaf(a[i].z, b[j].w, ci[i][j]);
+      ci[i][j] = fmaf(a[i].w, b[j].z, ci[i][j]);
+    }
+}
+
+template <int TM, int TN>
+__global__ void __launch_bounds__(DOT_THREADS, 2) cdot_blk_kernel(const float2* __restrict__ A,
+                                                                  const float2* __restrict__ B,
+                                                                  float2* __restrict__ part, int M, int N, int K,
+                                                                  int kchunk) {
+  __shared__ float red[DOT_THREADS / 32][2 * 64];
   const int split = blockIdx.x, h = blockIdx.y;
   const int kbeg = split * kchunk, kend = min(K, kbeg + kchunk);
-  const float2* Ah = A + size_t(h) * M * K;
-  const float2* Bh = B + size_t(h) * N * K;
-  float cr[MX][MX], ci[MX][MX];
+  const int nbj = N / TN, nb = (M / TM) * nbj;  // nb in {1, 2, 4}
+  const int blk = threadIdx.x & (nb - 1), kq = threadIdx.x / nb;
+  const int bi = blk / nbj, bj = blk % nbj;
+  const int step = 2 * (DOT_THREADS / nb);  // K values one CTA iteration covers
+  const float2* Ar = A + size_t(h) * M * K + size_t(bi * TM) * K;
+  const float2* Br = B + size_t(h) * N * K + size_t(bj * TN) * K;
+  float cr[TM][TN], ci[TM][TN];
 #pragma unroll
-  for (int i = 0; i < MX; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < MX; ++j) cr[i][j] = ci[i][j] = 0.f;
-  // two complex values per 16-byte load (kbeg is even because kchunk is)
-  for (int k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * DOT_THREADS) {
-    const bool two = k + 1 < kend;
-    float4 a[MX], b[MX];
-#pragma unroll
-    for (int i = 0; i < MX; ++i) {
-      a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      b[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < M) {
-        if (two) a[i] = *reinterpret_cast<const float4*>(Ah + size_t(i) * K + k);
-        else { float2 v = Ah[size_t(i) * K + k]; a[i].x = v.x; a[i].y = v.y; }
-      }
-      if (i < N) {
-        if (two) b[i] = *reinterpret_cast<const float4*>(Bh + size_t(i) * K + k);
-        else { float2 v = Bh[size_t(i) * K + k]; b[i].x = v.x; b[i].y = v.y; }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < MX; ++i)
-#pragma unroll
-      for (int j = 0; j < MX; ++j) {
-        cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
-        cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
-        ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
-        ci[i][j] = fmaf(a[i].y, b[j].x, ci[i][j]);
-        cr[i][j] = fmaf(a[i].z, b[j].z, cr[i][j]);
-        cr[i][j] = fmaf(-a[i].w, b[j].w, cr[i][j]);
-        ci[i][j] = fmaf(a[i].z, b[j].w, ci[i][j]);
-        ci[i][j] = fmaf(a[i].w, b[j].z, ci[i][j]);
-      }
+    for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0.f;
+  // kbeg is even (kchunk is), so every 16-byte load is aligned when K is even
+  for (int k = kbeg + 2 * kq; k < kend; k += 2 * step) {
+    float4 a0[TM], b0[TN], a1[TM], b1[TN];
+    cdot_load<TM, TN>(Ar, Br, K, k, kend, a0, b0);
+    cdot_load<TM, TN>(Ar, Br, K, k + step, kend, a1, b1);
+    cdot_fma<TM, TN>(a0, b0, cr, ci);
+    cdot_fma<TM, TN>(a1, b1, cr, ci);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < MX; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < MX; ++j) {
+    for (int j = 0; j < TN; ++j) {
       float r = cr[i][j], im = ci[i][j];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
+      // sum over the lanes of the same block (lane bits above the block bits)
+      for (int off = 16; off >= nb; off >>= 1) {
         r += __shfl_xor_sync(0xffffffffu, r, off);
         im += __shfl_xor_sync(0xffffffffu, im, off);
       }
-      if (lane == 0) {
-        red[warp][2 * (i * MX + j)] = r;
-        red[warp][2 * (i * MX + j) + 1] = im;
+      if (lane < nb) {
+        red[warp][2 * (lane * TM * TN + i * TN + j)] = r;
+        red[warp][2 * (lane * TM * TN + i * TN + j) + 1] = im;
       }
     }
   __syncthreads();
-  for (int q = threadIdx.x; q < 2 * MX * MX; q += DOT_THREADS) {
+  for (int q = threadIdx.x; q < 2 * M * N; q += DOT_THREADS) {
     float v = 0.f;
     for (int w = 0; w < DOT_THREADS / 32; ++w) v += red[w][q];
-    const int ij = q >> 1, i = ij / MX, j = ij % MX;
-    if (i < M && j < N) {
-      float* dst = reinterpret_cast<float*>(part + (size_t(split) * gridDim.y + h) * M * N + size_t(i) * N + j);
-      dst[q & 1] = v;
-    }
+    const int b = q / (2 * TM * TN), ij = (q % (2 * TM * TN)) >> 1;
+    const int i = (b / nbj) * TM + ij / TN, j = (b % nbj) * TN + ij % TN;
+    float* dst = reinterpret_cast<float*>(part + (size_t(split) * gridDim.y + h) * M * N + size_t(i) * N + j);
+    dst[q & 1] = v;
   }
 }
 
 // Small operand of ns <= 32 rows and K <= 32: each thread owns one row of the
 // large operand and reads it with 16-byte loads straight into registers.
-template <int KMAX>
+template <int KMAX, int ROWS>
 __global__ void __launch_bounds__(256) cgemm_rows_regk_kernel(const float2* __restrict__ S, const float2* __restrict__ G,
                                                               float2* __restrict__ C, double2* __restrict__ acc, int ns,
                                                               int ng, int K, int batch, long long s_stride,
                                                               long long g_stride, int tiles_g) {
+  // ROWS rows of the large operand per thread (256 * ROWS per CTA): each small-
+  // operand value read from shared memory serves ROWS multiply-adds
   __shared__ float2 Ss[RW_SMAX][KMAX];
   const int tile = int(blockIdx.x % tiles_g);
   const int h = int(blockIdx.x / tiles_g);
@@ -189,46 +212,61 @@ __global__ void __launch_bounds__(256) cgemm_rows_regk_kernel(const float2* __re
     Ss[r][kk] = (r < ns && kk < K) ? Sh[size_t(r) * K + kk] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int g = tile * blockDim.x + threadIdx.x;
-  if (g >= ng) return;
-  const float2* row = G + size_t(h) * ng * K + size_t(g) * K;
-  float2 gv[KMAX];
-  if ((K & 1) == 0) {
+  int g[ROWS];
+  bool live[ROWS];
+  float2 gv[ROWS][KMAX];
 #pragma unroll
-    for (int kk = 0; kk < KMAX; kk += 2)
-      if (kk < K) {
-        const float4 v = *reinterpret_cast<const float4*>(row + kk);
-        gv[kk] = make_float2(v.x, v.y);
-        gv[kk + 1] = make_float2(v.z, v.w);
-      }
-  } else {
+  for (int r = 0; r < ROWS; ++r) {
+    g[r] = tile * 256 * ROWS + r * 256 + threadIdx.x;
+    live[r] = g[r] < ng;
+    const float2* row = G + size_t(h) * ng * K + size_t(live[r] ? g[r] : 0) * K;
+    if ((K & 1) == 0) {
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk)
-      if (kk < K) gv[kk] = row[kk];
+      for (int kk = 0; kk < KMAX; kk += 2)
+        if (kk < K) {
+          const float4 v = live[r] ? *reinterpret_cast<const float4*>(row + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
+          gv[r][kk] = make_float2(v.x, v.y);
+          gv[r][kk + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < KMAX; ++kk)
+        if (kk < K) gv[r][kk] = live[r] ? row[kk] : make_float2(0.f, 0.f);
+    }
   }
   const size_t hbase = size_t(h) * ns * ng;
 #pragma unroll
   for (int s = 0; s < RW_SMAX; ++s) {
     if (s >= ns) break;
-    float ar = 0.f, ai = 0.f;
+    float ar[ROWS], ai[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) ar[r] = ai[r] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < KMAX; ++kk) {
       if (kk < K) {
-        const float2 a = Ss[s][kk], b = gv[kk];
-        ar = fmaf(a.x, b.x, ar);
-        ar = fmaf(-a.y, b.y, ar);
-        ai = fmaf(a.x, b.y, ai);
-        ai = fmaf(a.y, b.x, ai);
+        const float2 a = Ss[s][kk];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const float2 bb = gv[r][kk];
+          ar[r] = fmaf(a.x, bb.x, ar[r]);
+          ar[r] = fmaf(-a.y, bb.y, ar[r]);
+          ai[r] = fmaf(a.x, bb.y, ai[r]);
+          ai[r] = fmaf(a.y, bb.x, ai[r]);
+        }
       }
     }
-    const size_t o = hbase + size_t(s) * s_stride + size_t(g) * g_stride;
-    if (acc) {
-      double2 v = acc[o];
-      v.x += ar;
-      v.y += ai;
-      acc[o] = v;
-    } else {
-      C[o] = make_float2(ar, ai);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      if (!live[r]) continue;
+      const size_t o = hbase + size_t(s) * s_stride + size_t(g[r]) * g_stride;
+      if (acc) {
+        double2 v = acc[o];
+        v.x += ar[r];
+        v.y += ai[r];
+        acc[o] = v;
+      } else {
+        C[o] = make_float2(ar[r], ai[r]);
+      }
     }
   }
 }
@@ -237,7 +275,7 @@ __global__ void __launch_bounds__(256) cgemm_rows_regk_kernel(const float2* __re
 // layout (no separate permute): row g (its N or M index, then batch bits) starts
 // at the source offset sum_j bit_j(g) << rowpos[j], and element k of a row is
 // koff[k] further on.  Leaves with sliced labels add the slice offset.
-template <int KMAX>
+template <int KMAX, int ROWS>
 __global__ void __launch_bounds__(256) cgemm_rows_gather_kernel(const float2* __restrict__ S,
                                                                 const float2* __restrict__ G, const GatherDesc gd,
                                                                 float2* __restrict__ C, double2* __restrict__ acc,
@@ -258,55 +296,73 @@ __global__ void __launch_bounds__(256) cgemm_rows_gather_kernel(const float2* __
       if ((kk >> j) & 1) o |= 1u << gd.kpos[j];
     koff[kk] = o;
   }
-  __syncthreads();
-  const int g = tile * blockDim.x + threadIdx.x;
-  if (g >= ng) return;
-  // global row index over (g, h): g's bits first, then the batch bits
-  const long long grow = (long long)h * ng + g;
-  size_t base = 0;
-  for (int j = 0; j < gd.nrow; ++j)
-    if ((grow >> j) & 1) base |= size_t(1) << gd.rowpos[j];
+  size_t soff = 0;
   for (int j = 0; j < gd.n_slice; ++j)
-    if (gd.slice_src[j] >= 0 && ((slice_id >> j) & 1)) base |= size_t(1) << gd.slice_src[j];
-  float2 gv[KMAX];
-  if (gd.nk >= 1 && gd.kpos[0] == 0) {
-    // the lowest K bit is the stored layout's stride-1 bit: pairs (k, k+1) are
-    // adjacent and 16-byte aligned (every other offset bit is >= 1)
+    if (gd.slice_src[j] >= 0 && ((slice_id >> j) & 1)) soff |= size_t(1) << gd.slice_src[j];
+  __syncthreads();
+  const bool pairs = gd.nk >= 1 && gd.kpos[0] == 0;
+  int g[ROWS];
+  bool live[ROWS];
+  float2 gv[ROWS][KMAX];
 #pragma unroll
-    for (int kk = 0; kk < KMAX; kk += 2)
-      if (kk < K) {
-        const float4 v = *reinterpret_cast<const float4*>(G + base + koff[kk]);
-        gv[kk] = make_float2(v.x, v.y);
-        gv[kk + 1] = make_float2(v.z, v.w);
-      }
-  } else {
+  for (int r = 0; r < ROWS; ++r) {
+    g[r] = tile * 256 * ROWS + r * 256 + threadIdx.x;
+    live[r] = g[r] < ng;
+    // global row index over (g, h): g's bits first, then the batch bits
+    const long long grow = (long long)h * ng + (live[r] ? g[r] : 0);
+    size_t base = soff;
+    for (int j = 0; j < gd.nrow; ++j)
+      if ((grow >> j) & 1) base |= size_t(1) << gd.rowpos[j];
+    if (pairs) {
+      // the lowest K bit is the stored layout's stride-1 bit: pairs (k, k+1) are
+      // adjacent and 16-byte aligned (every other offset bit is >= 1)
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk)
-      if (kk < K) gv[kk] = G[base + koff[kk]];
+      for (int kk = 0; kk < KMAX; kk += 2)
+        if (kk < K) {
+          const float4 v = live[r] ? *reinterpret_cast<const float4*>(G + base + koff[kk])
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+          gv[r][kk] = make_float2(v.x, v.y);
+          gv[r][kk + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < KMAX; ++kk)
+        if (kk < K) gv[r][kk] = live[r] ? G[base + koff[kk]] : make_float2(0.f, 0.f);
+    }
   }
   const size_t hbase = size_t(h) * ns * ng;
 #pragma unroll
   for (int s = 0; s < RW_SMAX; ++s) {
     if (s >= ns) break;
-    float ar = 0.f, ai = 0.f;
+    float ar[ROWS], ai[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) ar[r] = ai[r] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < KMAX; ++kk) {
       if (kk < K) {
-        const float2 a = Ss[s][kk], b = gv[kk];
-        ar = fmaf(a.x, b.x, ar);
-        ar = fmaf(-a.y, b.y, ar);
-        ai = fmaf(a.x, b.y, ai);
-        ai = fmaf(a.y, b.x, ai);
+        const float2 a = Ss[s][kk];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const float2 bb = gv[r][kk];
+          ar[r] = fmaf(a.x, bb.x, ar[r]);
+          ar[r] = fmaf(-a.y, bb.y, ar[r]);
+          ai[r] = fmaf(a.x, bb.y, ai[r]);
+          ai[r] = fmaf(a.y, bb.x, ai[r]);
+        }
       }
     }
-    const size_t o = hbase + size_t(s) * s_stride + size_t(g) * g_stride;
-    if (acc) {
-      double2 v = acc[o];
-      v.x += ar;
-      v.y += ai;
-      acc[o] = v;
-    } else {
-      C[o] = make_float2(ar, ai);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      if (!live[r]) continue;
+      const size_t o = hbase + size_t(s) * s_stride + size_t(g[r]) * g_stride;
+      if (acc) {
+        double2 v = acc[o];
+        v.x += ar[r];
+        v.y += ai[r];
+        acc[o] = v;
+      } else {
+        C[o] = make_float2(ar[r], ai[r]);
+      }
     }
   }
 }
@@ -317,7 +373,8 @@ cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const
                                      int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
                                      int slice_id, cudaStream_t st) {
   if (ns < 1 || ns > RW_SMAX || K > 32 || gd.nrow > 32 || gd.nk > 5) return cudaErrorInvalidConfiguration;
-  const long long tg = (ng + 255) / 256;
+  const int rows = K <= 16 ? 2 : 1;  // rows per thread
+  const long long tg = (ng + 256 * rows - 1) / (256 * rows);
   if (tg * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const dim3 g2{unsigned(tg * batch), 1u, 1u};
   const float2* Sp = reinterpret_cast<const float2*>(Ssmall);
@@ -325,14 +382,14 @@ cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const
   float2* Cp = reinterpret_cast<float2*>(C);
   double2* Ap = reinterpret_cast<double2*>(acc);
   if (K <= 8)
-    cgemm_rows_gather_kernel<8><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out,
-                                                    int(tg), slice_id);
+    cgemm_rows_gather_kernel<8, 2><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
+                                                       g_stride_out, int(tg), slice_id);
   else if (K <= 16)
-    cgemm_rows_gather_kernel<16><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
-                                                     g_stride_out, int(tg), slice_id);
+    cgemm_rows_gather_kernel<16, 2><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
+                                                        g_stride_out, int(tg), slice_id);
   else
-    cgemm_rows_gather_kernel<32><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
-                                                     g_stride_out, int(tg), slice_id);
+    cgemm_rows_gather_kernel<32, 1><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
+                                                        g_stride_out, int(tg), slice_id);
   return cudaGetLastError();
 }
 
@@ -341,8 +398,9 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
                               cudaStream_t st) {
   if (ns < 1 || ns > RW_SMAX || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
   if (K <= 32 && splits == 1) {
-    // short rows: register-resident row of the large operand
-    const long long tg = (ng + 255) / 256;
+    // short rows: register-resident rows of the large operand
+    const int rows = K <= 16 ? 2 : 1;
+    const long long tg = (ng + 256 * rows - 1) / (256 * rows);
     if (tg * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const dim3 g2{unsigned(tg * batch), 1u, 1u};
     const float2* Sp = reinterpret_cast<const float2*>(Ssmall);
@@ -350,11 +408,11 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
     float2* Cp = reinterpret_cast<float2*>(C);
     double2* Ap = reinterpret_cast<double2*>(acc);
     if (K <= 8)
-      cgemm_rows_regk_kernel<8><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
+      cgemm_rows_regk_kernel<8, 2><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
     else if (K <= 16)
-      cgemm_rows_regk_kernel<16><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
+      cgemm_rows_regk_kernel<16, 2><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
     else
-      cgemm_rows_regk_kernel<32><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
+      cgemm_rows_regk_kernel<32, 1><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
     return cudaGetLastError();
   }
   const long long tiles_g = (ng + RW_THREADS - 1) / RW_THREADS;
@@ -377,10 +435,15 @@ cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, in
   const float2* Ap = reinterpret_cast<const float2*>(A);
   const float2* Bp = reinterpret_cast<const float2*>(B);
   float2* Pp = reinterpret_cast<float2*>(part);
-  if (M <= 4 && N <= 4)
-    cdot_kernel<4><<<grid, DOT_THREADS, 0, st>>>(Ap, Bp, Pp, M, N, K, kchunk);
-  else
-    cdot_kernel<8><<<grid, DOT_THREADS, 0, st>>>(Ap, Bp, Pp, M, N, K, kchunk);
+  // M and N are powers of two (all-dim-2 tensors); K even keeps the 16-byte
+  // loads of every row aligned
+  if ((M & (M - 1)) || (N & (N - 1)) || (K & 1)) return cudaErrorInvalidConfiguration;
+  const int tm = M < 4 ? M : 4, tn = N < 4 ? N : 4;
+#define TNQ_DOT(TM_, TN_) \
+  if (tm == TM_ && tn == TN_) cdot_blk_kernel<TM_, TN_><<<grid, DOT_THREADS, 0, st>>>(Ap, Bp, Pp, M, N, K, kchunk)
+  TNQ_DOT(1, 1); else TNQ_DOT(1, 2); else TNQ_DOT(1, 4); else TNQ_DOT(2, 1); else TNQ_DOT(2, 2);
+  else TNQ_DOT(2, 4); else TNQ_DOT(4, 1); else TNQ_DOT(4, 2); else TNQ_DOT(4, 4);
+#undef TNQ_DOT
   return cudaGetLastError();
 }
 

@@ -47,7 +47,8 @@ def rel(a, b):
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("mnk", [(2, 3, 4), (6, 6, 6), (7, 5, 8), (3, 9, 10), (8, 8, 2), (6, 8, 10),
                                  (2, 2, 18), (0, 1, 16), (5, 6, 14), (9, 4, 12), (3, 3, 14), (3, 2, 12),
-                                 (4, 10, 5), (2, 12, 0), (12, 3, 3), (5, 12, 5), (12, 5, 4), (1, 13, 3)])
+                                 (4, 10, 5), (2, 12, 0), (12, 3, 3), (5, 12, 5), (12, 5, 4), (1, 13, 3),
+                                 (3, 18, 3), (17, 4, 4), (5, 16, 5), (0, 15, 2)])
 def test_full_output(T, prec, mnk):
     m, n, k = mnk
     al, bl, ol, A, B = microbench_case(m, n, k, seed=m * 100 + n * 10 + k)
@@ -81,6 +82,24 @@ def test_batch_labels(T, prec):
     C = _run(T, prec, A, al, B, bl, ol)
     ref = contraction.contract_labeled(A, al, B, bl, ol)
     assert rel(C, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16x3"])
+def test_tall_skinny_batch(T, prec):
+    """A tall-skinny step with batch labels (2^3 x 2^14 output per batch entry,
+    K = 2^3, 2^2 batch entries, every operand's bits scattered): the large
+    operand is gathered in place and the small one expanded per batch entry."""
+    rng = np.random.default_rng(11)
+    small, big, kl, hl = [10, 11, 12], list(range(20, 34)), [0, 1, 2], [100, 101]
+    al = list(rng.permutation(small + kl + hl))
+    bl = list(rng.permutation(big + kl + hl))
+    ol = list(rng.permutation(small + big + hl))
+    A = (rng.standard_normal(2 ** 8) + 1j * rng.standard_normal(2 ** 8)).astype(np.complex64)
+    B = (rng.standard_normal(2 ** 19) + 1j * rng.standard_normal(2 ** 19)).astype(np.complex64)
+    C = _run(T, prec, A, al, B, bl, ol)
+    ref = contraction.contract_labeled(A, al, B, bl, ol)
+    assert np.all(np.isfinite(C))
+    assert rel(C, ref) <= TOL[prec], (prec, rel(C, ref))
 
 
 def test_invalid_labels_rejected(T):
