@@ -1,12 +1,13 @@
 // Tall-skinny complex GEMM on the tcgen05 tensor cores, sm_103a.
 //
 // Steps of the contraction sequence (Sec. 3.1) whose one operand is small
-// (ns <= 32 rows) and whose contracted extent is short (K <= 32) but whose
+// (ns <= 64 rows) and whose contracted extent is short (K <= 64) but whose
 // other operand G is large (ng rows, up to 2^24 and more) do 8 * ns real flops
 // per byte of G: too few for a tensor-core tile built the ordinary way (the
-// 2 * ns-row expansion of the small operand would fill a quarter of a 128-row
-// MMA), too many for the CUDA cores to keep up with HBM.  Here the roles are
-// swapped: 128 rows of G form the MMA's M side, the expanded small operand
+// 2 * ns-row expansion of the small operand would fill part of a 128-row MMA
+// and the large operand would need a permute and a separate hi/lo split), too
+// many for the CUDA cores to keep up with HBM.  Here the roles are swapped:
+// 128 rows of G form the MMA's M side, the expanded small operand
 //   S' (2 ns x 2K):  row (s, re) = [sr_0, -si_0, sr_1, -si_1, ...]
 //                    row (s, im) = [si_0,  sr_0, si_1,  sr_1, ...]
 // its N side, and D = G * S'^T leaves Re/Im of out[s][g] in TMEM columns
@@ -15,20 +16,22 @@
 // G is read once from HBM, in its stored bit order (the gather of the permute
 // is fused: the row and K bits of G sit at arbitrary positions of the stored
 // tensor), split into hi/lo parts (BF16 or TF32) by converter warps and written
-// straight into the 128-byte-swizzled K-major layout the MMA reads.  The
-// output is written once.  Per 128-row tile: 128 * K * 8 bytes in, 128 * ns * 8
-// bytes out, 3 * ceil(2K / k_step) MMAs of 128 x Npad (Npad = max(16, 2 ns)).
+// straight into the 128-byte-swizzled K-major layout the MMA reads (one or two
+// 128-byte swizzle atoms per row).  The output is written once.  Per 128-row
+// tile: 128 * K * 8 bytes in, 128 * ns * 8 bytes out, 3 * ceil(2K / k_step)
+// MMAs of 128 x Npad (Npad = max(16, 2 ns)).
 //
 // CTA (persistent, one per SM) = 13 warps:
 //   warps 0-7   converters, two groups of four; group g fills the stages of
 //               the CTA's tiles i = g, g + 2, ...: each thread owns one tile
-//               row, loads it (16-byte pairs when the lowest stored bit is a
-//               K bit), splits it, stores it swizzled, and prefetches its row
-//               of the group's next tile before waiting for a free stage;
+//               row and walks it in chunks of up to 16 complex values (loads
+//               of 16-byte pairs when the lowest stored bit is a K bit),
+//               splitting and storing one chunk while the next is in flight;
 //   warp 8      allocates TMEM and (one thread) issues the MMAs of each tile
-//               into one of NACC accumulator buffers;
-//   warps 9-12  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and writes
-//               complex64 outputs (or adds into the FP64 cross-slice sum).
+//               into one of the TMEM accumulator buffers;
+//   warps 9-12  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, 32
+//               columns at a time, and writes complex64 outputs (or adds into
+//               the FP64 cross-slice sum).
 // Every mbarrier wait is bounded; one that runs out sets the error flag and
 // the CTA unwinds.
 #include <cuda_bf16.h>
@@ -51,11 +54,13 @@ using namespace tcx;
 constexpr int TR_CONV_WARPS = 8;
 constexpr int TR_THREADS = 32 * (TR_CONV_WARPS + 1 + 4);
 constexpr int TR_MMA_WARP = TR_CONV_WARPS;
-constexpr int TR_STAGES = 4;      // even: stage parity = converter group
-constexpr int TR_NACC = 4;        // TMEM accumulator buffers
-constexpr int TR_ROW_BYTES = 128; // one swizzle atom per tile row (all of K)
-constexpr int TR_STAGE_BYTES = 2 * 128 * TR_ROW_BYTES;  // hi + lo
+constexpr int TR_MAX_STAGES = 4;               // even: stage parity = converter group
+constexpr int TR_MAX_NACC = 4;                 // TMEM accumulator buffers
+constexpr int TR_ROW_BYTES = 128;              // one swizzle atom of a row
+constexpr int TR_ATOM_BYTES = 128 * TR_ROW_BYTES;  // one atom column of a 128-row tile
+constexpr int TR_STAGE_BUDGET = 128 * 1024;
 constexpr int TR_BPRIME_BUDGET = 64 * 1024;
+constexpr int TR_KMAX = 64;
 
 struct TrParams {
   const float2* S;        // small operand [batch][ns][K]
@@ -64,6 +69,10 @@ struct TrParams {
   int ns, ng, K, batch;
   int npad;               // MMA N: max(16, 2 ns)
   int nks;                // MMA K steps (32 bytes of K per step)
+  int atoms;              // 128-byte swizzle atoms per row (1 or 2)
+  int stages;             // shared-memory stages (4 with one atom, 2 with two)
+  int nacc;               // TMEM accumulator buffers
+  int nchunks;            // converter chunks per row
   int kind_bf16;          // 1: BF16 parts, kind::f16; 0: TF32 parts, kind::tf32
   int split;              // 1: three products (hi/lo); 0: one TF32 product
   int pairs;              // the lowest stored bit of G is K bit 0: 16-byte loads
@@ -97,59 +106,65 @@ __device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t* hi, ui
   *lo = l0 | (l1 << 16);
 }
 
-// Byte offset of 16-byte chunk j of row r in a 128-byte-swizzled K-major tile
-// (8-row groups of 1024 bytes; chunk index XOR row-in-group).
-__device__ __forceinline__ uint32_t swz(int r, int j) { return uint32_t(r) * 128u + (uint32_t(j ^ (r & 7)) << 4); }
+// Byte offset of 16-byte unit u of row r in a K-major tile of 128-byte-swizzled
+// atoms: atom u / 8 (atom columns atom_bytes apart), 8-row groups of 1024 bytes
+// within an atom, unit index XOR row-in-group.
+__device__ __forceinline__ uint32_t swz(int r, int u, uint32_t atom_bytes) {
+  return uint32_t(u >> 3) * atom_bytes + uint32_t(r) * 128u + (uint32_t((u & 7) ^ (r & 7)) << 4);
+}
 
-// Split the 2K reals of one row (complex v[0..K-1], zero beyond K) and store the
-// first nks * 32 bytes of its hi and lo rows.
-template <int KMAX>
-__device__ __forceinline__ void store_row(uint8_t* hi, uint8_t* lo, int r, const float2 (&v)[KMAX], int nks,
-                                          int kind_bf16, int split) {
+// Split chunk c (complex values c*CH .. c*CH+CH-1 of the row, zero beyond K)
+// and store its 16-byte units that the MMAs read (units < 2 * nks).
+template <int CH>
+__device__ __forceinline__ void store_chunk(uint8_t* hi, uint8_t* lo, int r, const float2 (&v)[CH], int c,
+                                            int units, int kind_bf16, int split) {
   if (kind_bf16) {
-    // chunk j: complex 4j .. 4j+3 (8 BF16 reals); two chunks per 32-byte K step
+    // one unit: 4 complex values (8 BF16 reals)
 #pragma unroll
-    for (int j = 0; j < KMAX / 4; ++j) {
-      if (j < 2 * nks) {
+    for (int j = 0; j < CH / 4; ++j) {
+      const int u = c * (CH / 4) + j;
+      if (u < units) {
         uint4 h, l;
         bf16_split2(v[4 * j].x, v[4 * j].y, &h.x, &l.x);
         bf16_split2(v[4 * j + 1].x, v[4 * j + 1].y, &h.y, &l.y);
         bf16_split2(v[4 * j + 2].x, v[4 * j + 2].y, &h.z, &l.z);
         bf16_split2(v[4 * j + 3].x, v[4 * j + 3].y, &h.w, &l.w);
-        *reinterpret_cast<uint4*>(hi + swz(r, j)) = h;
-        *reinterpret_cast<uint4*>(lo + swz(r, j)) = l;
+        *reinterpret_cast<uint4*>(hi + swz(r, u, TR_ATOM_BYTES)) = h;
+        *reinterpret_cast<uint4*>(lo + swz(r, u, TR_ATOM_BYTES)) = l;
       }
     }
   } else {
-    // chunk j: complex 2j, 2j+1 (4 TF32 reals); two chunks per 32-byte K step
+    // one unit: 2 complex values (4 TF32 reals)
 #pragma unroll
-    for (int j = 0; j < KMAX / 2; ++j) {
-      if (j < 2 * nks) {
+    for (int j = 0; j < CH / 2; ++j) {
+      const int u = c * (CH / 2) + j;
+      if (u < units) {
         float4 h, l;
         h.x = tf32_rna(v[2 * j].x);
         h.y = tf32_rna(v[2 * j].y);
         h.z = tf32_rna(v[2 * j + 1].x);
         h.w = tf32_rna(v[2 * j + 1].y);
-        *reinterpret_cast<float4*>(hi + swz(r, j)) = h;
+        *reinterpret_cast<float4*>(hi + swz(r, u, TR_ATOM_BYTES)) = h;
         if (split) {
           l.x = tf32_rna(v[2 * j].x - h.x);
           l.y = tf32_rna(v[2 * j].y - h.y);
           l.z = tf32_rna(v[2 * j + 1].x - h.z);
           l.w = tf32_rna(v[2 * j + 1].y - h.w);
-          *reinterpret_cast<float4*>(lo + swz(r, j)) = l;
+          *reinterpret_cast<float4*>(lo + swz(r, u, TR_ATOM_BYTES)) = l;
         }
       }
     }
   }
 }
 
-// Expanded small operand S' for every batch entry: rows n < npad of 2K reals,
-// hi and lo, built by the converter threads at kernel start.
+// Expanded small operand S' for every batch entry: rows n < npad of the reals
+// the MMAs read, hi and lo, built by the converter threads at kernel start.
 __device__ void build_bprime(const TrParams& P, uint8_t* bp, int tid, int nthreads) {
   const int es = P.kind_bf16 ? 2 : 4;
-  const int reals = P.nks * (32 / es);  // reals per row the MMAs read
+  const int reals = P.nks * (32 / es);
   const int per_h = P.npad * reals;
-  const uint32_t half_bytes = uint32_t(P.npad) * TR_ROW_BYTES;
+  const uint32_t atom_bytes = uint32_t(P.npad) * TR_ROW_BYTES;
+  const uint32_t half_bytes = atom_bytes * P.atoms;
   for (int e = tid; e < P.batch * per_h; e += nthreads) {
     const int h = e / per_h, rem = e % per_h, n = rem / reals, q = rem % reals;
     const int s = n >> 1, k = q >> 1;
@@ -161,7 +176,7 @@ __device__ void build_bprime(const TrParams& P, uint8_t* bp, int tid, int nthrea
     }
     uint8_t* hi = bp + size_t(h) * 2 * half_bytes;
     uint8_t* lo = hi + half_bytes;
-    const uint32_t off = swz(n, (q * es) >> 4) + uint32_t((q * es) & 15);
+    const uint32_t off = swz(n, (q * es) >> 4, atom_bytes) + uint32_t((q * es) & 15);
     if (P.kind_bf16) {
       const uint32_t hb = bf16_bits(x);
       *reinterpret_cast<unsigned short*>(hi + off) = (unsigned short)hb;
@@ -174,12 +189,6 @@ __device__ void build_bprime(const TrParams& P, uint8_t* bp, int tid, int nthrea
   }
 }
 
-// Row r of tile t: (batch entry, first row) and the stored offset of its K = 0
-// element, from the row bits' positions (bits 0-6 of the row index are r).
-struct RowAddr {
-  size_t lo;  // r's bits deposited at rowpos[0..6]
-};
-
 __device__ __forceinline__ size_t deposit(long long v, const int* pos, int n) {
   size_t o = 0;
   for (int j = 0; j < n; ++j)
@@ -187,52 +196,57 @@ __device__ __forceinline__ size_t deposit(long long v, const int* pos, int n) {
   return o;
 }
 
-template <int KMAX>
-__device__ __forceinline__ void load_row(const TrParams& P, const uint32_t* koff, size_t base, float2 (&v)[KMAX]) {
+// Chunk c of the row whose K = 0 element sits at stored offset `base`.
+template <int CH>
+__device__ __forceinline__ void load_chunk(const TrParams& P, const uint32_t* koff, size_t base, int c,
+                                           float2 (&v)[CH]) {
+  const int k0 = c * CH;
   if (P.pairs) {
 #pragma unroll
-    for (int kk = 0; kk < KMAX; kk += 2) {
+    for (int j = 0; j < CH; j += 2) {
       float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (kk < P.K) t = __ldg(reinterpret_cast<const float4*>(P.G + base + koff[kk]));
-      v[kk] = make_float2(t.x, t.y);
-      v[kk + 1] = make_float2(t.z, t.w);
+      if (k0 + j < P.K) t = __ldg(reinterpret_cast<const float4*>(P.G + base + koff[k0 + j]));
+      v[j] = make_float2(t.x, t.y);
+      v[j + 1] = make_float2(t.z, t.w);
     }
   } else {
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) v[kk] = kk < P.K ? __ldg(P.G + base + koff[kk]) : make_float2(0.f, 0.f);
+    for (int j = 0; j < CH; ++j) v[j] = k0 + j < P.K ? __ldg(P.G + base + koff[k0 + j]) : make_float2(0.f, 0.f);
   }
 }
 
-template <int KMAX>
+template <int CH>
 __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __grid_constant__ TrParams P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[TR_STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[TR_STAGES];
-  __shared__ __align__(8) uint64_t acc_full[TR_NACC];
-  __shared__ __align__(8) uint64_t acc_empty[TR_NACC];
+  __shared__ __align__(8) uint64_t full_bar[TR_MAX_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[TR_MAX_STAGES];
+  __shared__ __align__(8) uint64_t acc_full[TR_MAX_NACC];
+  __shared__ __align__(8) uint64_t acc_empty[TR_MAX_NACC];
   __shared__ __align__(8) uint64_t final_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ uint32_t koff[KMAX];
+  __shared__ uint32_t koff[TR_KMAX];
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* bprime = smem + TR_STAGES * TR_STAGE_BYTES;
-  const uint32_t bp_half = uint32_t(P.npad) * TR_ROW_BYTES;
+  const uint32_t stage_bytes = 2u * TR_ATOM_BYTES * uint32_t(P.atoms);  // hi + lo
+  uint8_t* bprime = smem + size_t(P.stages) * stage_bytes;
+  const uint32_t bp_atom = uint32_t(P.npad) * TR_ROW_BYTES;
+  const uint32_t bp_half = bp_atom * uint32_t(P.atoms);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t tmem_cols = uint32_t(P.npad * TR_NACC) < 32u ? 32u : uint32_t(P.npad * TR_NACC);
+  const uint32_t tmem_cols = uint32_t(P.npad * P.nacc) < 32u ? 32u : uint32_t(P.npad * P.nacc);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TR_STAGES; ++s) {
+    for (int s = 0; s < P.stages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 128);  // one converter group
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    for (int b = 0; b < TR_NACC; ++b) {
+    for (int b = 0; b < P.nacc; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
       mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&final_bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int kk = threadIdx.x; kk < KMAX; kk += blockDim.x) {
+  for (int kk = threadIdx.x; kk < TR_KMAX; kk += blockDim.x) {
     uint32_t o = 0;
     for (int j = 0; j < P.gd.nk; ++j)
       if ((kk >> j) & 1) o |= 1u << P.gd.kpos[j];
@@ -251,71 +265,104 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const long long stride = gridDim.x;
 
   if (warp < TR_CONV_WARPS) {
     // ---------------- converters: group grp fills the stages of tiles grp, grp+2, ...
     const int grp = warp >> 2, r = (warp & 3) * 32 + lane;
     const int nhi = P.gd.nrow - 7;
+    const int nch = P.nchunks, units = 2 * P.nks;
     size_t soff = 0;
     for (int j = 0; j < P.gd.n_slice; ++j)
       if (P.gd.slice_src[j] >= 0 && ((P.slice_id >> j) & 1)) soff |= size_t(1) << P.gd.slice_src[j];
     const size_t lo = soff | deposit(r, P.gd.rowpos, 7);
-    auto row_base = [&](long long t) {
-      const long long h = t / P.tiles_per_h, g0 = (t % P.tiles_per_h) * 128;
-      return lo | deposit((h * P.ng + g0) >> 7, P.gd.rowpos + 7, nhi);
+    const uint32_t tph = uint32_t(P.tiles_per_h), total = uint32_t(P.total_tiles), stride2 = 2u * gridDim.x;
+    auto row_base = [&](uint32_t t) {
+      const uint32_t h = t / tph, g0 = (t - h * tph) * 128u;
+      return lo | deposit(((long long)h * P.ng + g0) >> 7, P.gd.rowpos + 7, nhi);
     };
-    float2 cur[KMAX], nxt[KMAX];
-    long long i = grp;
-    long long t = blockIdx.x + i * stride;
-    if (t < P.total_tiles) load_row<KMAX>(P, koff, row_base(t), cur);
-    for (; t < P.total_tiles; i += 2, t += 2 * stride) {
-      const long long tn = t + 2 * stride;
-      if (tn < P.total_tiles) load_row<KMAX>(P, koff, row_base(tn), nxt);
-      const int s = int(i % TR_STAGES);
-      const uint32_t use = uint32_t(i / TR_STAGES);
-      if (!mbar_wait(smem_u32(&empty_bar[s]), (use & 1) ^ 1)) {
+    // items (tile, chunk c) in order; the next item's loads are issued before
+    // the current one is split and stored.  Tile i of this CTA (global tile
+    // blockIdx.x + i * gridDim.x) uses stage i % stages, phase (i / stages) & 1.
+    float2 cur[CH], nxt[CH];
+    uint32_t t = blockIdx.x + uint32_t(grp) * gridDim.x;
+    int s = grp, c = 0;
+    uint32_t ph = 0;
+    size_t base = t < total ? row_base(t) : 0;
+    if (t < total) load_chunk<CH>(P, koff, base, 0, cur);
+    while (t < total) {
+      uint32_t t2 = t;
+      int c2 = c + 1;
+      size_t base2 = base;
+      if (c2 == nch) {
+        c2 = 0;
+        t2 = t + stride2;
+        base2 = t2 < total ? row_base(t2) : 0;
+      }
+      if (t2 < total) load_chunk<CH>(P, koff, base2, c2, nxt);
+      if (c == 0 && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
         atomicOr(P.err, 1);
         break;
       }
-      uint8_t* st = smem + size_t(s) * TR_STAGE_BYTES;
-      store_row<KMAX>(st, st + TR_STAGE_BYTES / 2, r, cur, P.nks, P.kind_bf16, P.split);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(smem_u32(&full_bar[s]));
+      uint8_t* st = smem + size_t(s) * stage_bytes;
+      store_chunk<CH>(st, st + stage_bytes / 2, r, cur, c, units, P.kind_bf16, P.split);
+      if (c == nch - 1) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&full_bar[s]));
+        s += 2;  // this group's next tile
+        if (s >= P.stages) {
+          s -= P.stages;
+          ph ^= 1;
+        }
+      }
 #pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) cur[kk] = nxt[kk];
+      for (int j = 0; j < CH; ++j) cur[j] = nxt[j];
+      t = t2;
+      c = c2;
+      base = base2;
     }
   } else if (warp == TR_MMA_WARP) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      long long i = 0;
-      for (long long t = blockIdx.x; t < P.total_tiles; t += stride, ++i) {
-        const int s = int(i % TR_STAGES), b = int(i % TR_NACC);
-        if (i >= TR_NACC && !mbar_wait(smem_u32(&acc_empty[b]), uint32_t(i / TR_NACC - 1) & 1)) {
+      const uint32_t tph = uint32_t(P.tiles_per_h), total = uint32_t(P.total_tiles);
+      int s = 0, b = 0;
+      uint32_t sph = 0, bph = 0;  // phases of the stage ring and of the accumulator ring
+      bool drained = false;       // every accumulator buffer has been used once
+      for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        if (drained && !mbar_wait(smem_u32(&acc_empty[b]), bph ^ 1)) {
           atomicOr(P.err, 1);
           break;
         }
-        if (!mbar_wait(smem_u32(&full_bar[s]), uint32_t(i / TR_STAGES) & 1)) {
+        if (!mbar_wait(smem_u32(&full_bar[s]), sph)) {
           atomicOr(P.err, 1);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int h = int(t / P.tiles_per_h);
-        const uint32_t a_hi = smem_u32(smem + size_t(s) * TR_STAGE_BYTES), a_lo = a_hi + TR_STAGE_BYTES / 2;
-        const uint32_t b_hi = smem_u32(bprime) + uint32_t(h) * 2 * bp_half, b_lo = b_hi + bp_half;
+        const uint32_t h = t / tph;
+        const uint32_t a_hi = smem_u32(smem + size_t(s) * stage_bytes), a_lo = a_hi + stage_bytes / 2;
+        const uint32_t b_hi = smem_u32(bprime) + h * 2 * bp_half, b_lo = b_hi + bp_half;
         const uint32_t d = tmem + uint32_t(b * P.npad);
         for (int kk = 0; kk < P.nks; ++kk) {
-          const uint32_t off = kk * 32;
+          const uint32_t ao = uint32_t(kk >> 2) * TR_ATOM_BYTES + uint32_t(kk & 3) * 32;
+          const uint32_t bo = uint32_t(kk >> 2) * bp_atom + uint32_t(kk & 3) * 32;
           if (P.split) {
-            mma_issue(P.kind_bf16, d, smem_desc(a_lo + off), smem_desc(b_hi + off), P.idesc, kk > 0 ? 1u : 0u);
-            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_lo + off), P.idesc, 1u);
-            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, 1u);
+            mma_issue(P.kind_bf16, d, smem_desc(a_lo + ao), smem_desc(b_hi + bo), P.idesc, kk > 0 ? 1u : 0u);
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_lo + bo), P.idesc, 1u);
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, 1u);
           } else {
-            mma_issue(P.kind_bf16, d, smem_desc(a_hi + off), smem_desc(b_hi + off), P.idesc, kk > 0 ? 1u : 0u);
+            mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, kk > 0 ? 1u : 0u);
           }
         }
         mma_commit(smem_u32(&empty_bar[s]));
         mma_commit(smem_u32(&acc_full[b]));
+        if (++s == P.stages) {
+          s = 0;
+          sph ^= 1;
+        }
+        if (++b == P.nacc) {
+          b = 0;
+          bph ^= 1;
+          drained = true;
+        }
       }
       mma_commit(smem_u32(&final_bar));
     }
@@ -325,43 +372,49 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
     const int quarter = warp & 3;
     const uint32_t lane_addr = uint32_t(quarter * 32) << 16;
     const int row = quarter * 32 + lane;
-    long long i = 0;
-    for (long long t = blockIdx.x; t < P.total_tiles; t += stride, ++i) {
-      const int b = int(i % TR_NACC);
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[b]), uint32_t(i / TR_NACC) & 1));
+    const uint32_t tph = uint32_t(P.tiles_per_h), total = uint32_t(P.total_tiles);
+    int b = 0;
+    uint32_t bph = 0;
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[b]), bph));
       if (!ok) {
         if (lane == 0) atomicOr(P.err, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t v[64];
+      const uint32_t h = t / tph;
+      const uint32_t g = (t - h * tph) * 128u + uint32_t(row);
+      const size_t obase = size_t(h) * P.ns * P.ng + size_t(g) * P.g_stride;
       const uint32_t base = tmem + lane_addr + uint32_t(b * P.npad);
-      TC_LD16(base, v);
-      if (P.npad > 16) TC_LD16(base + 16, (v + 16));
-      if (P.npad > 32) {
-        TC_LD16(base + 32, (v + 32));
-        TC_LD16(base + 48, (v + 48));
+      // 32 columns (16 outputs) at a time
+      for (int c0 = 0; c0 < P.npad; c0 += 32) {
+        uint32_t v[32];
+        TC_LD16(base + c0, v);
+        if (c0 + 16 < P.npad) TC_LD16(base + c0 + 16, (v + 16));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int s = c0 / 2 + j;
+          if (s < P.ns) {
+            const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
+            const size_t o = obase + size_t(s) * P.s_stride;
+            if (P.acc) {
+              double2 a = P.acc[o];
+              a.x += double(re);
+              a.y += double(im);
+              P.acc[o] = a;
+            } else {
+              P.C[o] = make_float2(re, im);
+            }
+          }
+        }
       }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
-      const long long h = t / P.tiles_per_h;
-      const long long g = (t % P.tiles_per_h) * 128 + row;
-      const size_t obase = size_t(h) * P.ns * P.ng + size_t(g) * P.g_stride;
-#pragma unroll
-      for (int s = 0; s < 32; ++s) {
-        if (s >= P.ns) break;
-        const float re = __uint_as_float(v[2 * s]), im = __uint_as_float(v[2 * s + 1]);
-        const size_t o = obase + size_t(s) * P.s_stride;
-        if (P.acc) {
-          double2 a = P.acc[o];
-          a.x += double(re);
-          a.y += double(im);
-          P.acc[o] = a;
-        } else {
-          P.C[o] = make_float2(re, im);
-        }
+      if (++b == P.nacc) {
+        b = 0;
+        bph ^= 1;
       }
     }
   }
@@ -382,11 +435,14 @@ namespace {
 
 int tr_npad(int ns) { return std::max(16, (2 * ns + 15) / 16 * 16); }
 
-size_t tr_smem_bytes(int ns, int batch) {
-  return size_t(TR_STAGES) * TR_STAGE_BYTES + size_t(batch) * 2 * tr_npad(ns) * TR_ROW_BYTES + 1024;
+// 128-byte swizzle atoms per row: 2K reals of 2 (BF16) or 4 (TF32) bytes
+int tr_atoms(int K, bool bf16) { return (2 * K * (bf16 ? 2 : 4) + TR_ROW_BYTES - 1) / TR_ROW_BYTES; }
+
+size_t tr_bprime_bytes(int ns, int K, int batch, bool bf16) {
+  return size_t(batch) * 2 * tr_atoms(K, bf16) * tr_npad(ns) * TR_ROW_BYTES;
 }
 
-constexpr size_t TR_SMEM_MAX = size_t(TR_STAGES) * TR_STAGE_BYTES + TR_BPRIME_BUDGET + 1024;
+constexpr size_t TR_SMEM_MAX = size_t(TR_STAGE_BUDGET) + TR_BPRIME_BUDGET + 1024;
 
 }  // namespace
 
@@ -398,25 +454,24 @@ cudaError_t tc_rows_prepare() {
     if (result == cudaSuccess)
       result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     int(TR_SMEM_MAX));
-    if (result == cudaSuccess)
-      result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int(TR_SMEM_MAX));
   });
   return result;
 }
 
 bool tc_rows_supported(int ns, int ng, int K, int batch, int nrow, int precision) {
   if (precision != TNQ_PREC_TF32 && precision != TNQ_PREC_TF32X3 && precision != TNQ_PREC_BF16X3) return false;
-  const int kmax = precision == TNQ_PREC_BF16X3 ? 32 : 16;  // 2K reals fit one 128-byte row
-  if (ns < 1 || ns > 32 || K < 1 || K > kmax || ng < 128 || (ng & 127) || batch < 1 || nrow < 7) return false;
-  return size_t(batch) * 2 * tr_npad(ns) * TR_ROW_BYTES <= size_t(TR_BPRIME_BUDGET);
+  const bool bf16 = precision == TNQ_PREC_BF16X3;
+  // rows of 2K reals span at most two swizzle atoms
+  if (ns < 1 || ns > 64 || K < 1 || K > (bf16 ? 64 : 32) || ng < 128 || (ng & 127) || batch < 1 || nrow < 7)
+    return false;
+  return tr_bprime_bytes(ns, K, batch, bf16) <= size_t(TR_BPRIME_BUDGET);
 }
 
 cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
                                  int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
                                  int precision, int* err, int sm_count, cudaStream_t st) {
   if (!tc_rows_supported(ns, ng, K, batch, gd.nrow, precision) || !err) return cudaErrorNotSupported;
-  if (gd.nk > 5 || gd.nrow > 32 || (1 << gd.nk) != K) return cudaErrorInvalidValue;
+  if (gd.nk > 6 || gd.nrow > 32 || (1 << gd.nk) != K) return cudaErrorInvalidValue;
   cudaError_t pe = tc_rows_prepare();
   if (pe != cudaSuccess) return pe;
   TrParams P;
@@ -432,11 +487,17 @@ cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const Gat
   P.split = precision == TNQ_PREC_TF32 ? 0 : 1;
   const int k_step = P.kind_bf16 ? 8 : 4;  // complex values per 32-byte MMA K step
   P.nks = (K + k_step - 1) / k_step;
+  P.atoms = tr_atoms(K, P.kind_bf16 != 0);
+  P.stages = P.atoms == 1 ? 4 : 2;
+  P.nacc = P.npad <= 64 ? 4 : 2;
+  const int ch = K <= 8 ? 8 : 16;
+  P.nchunks = (K + ch - 1) / ch;
   P.pairs = gd.nk >= 1 && gd.kpos[0] == 0;
   P.s_stride = s_stride_out;
   P.g_stride = g_stride_out;
   P.tiles_per_h = ng / 128;
   P.total_tiles = (long long)P.tiles_per_h * batch;
+  if (P.total_tiles + 2ll * std::max(1, sm_count) > 0xffffffffll) return cudaErrorNotSupported;  // 32-bit tile counters
   P.slice_id = slice_id;
   // instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1), K-major, N >> 3, M >> 4
   const uint32_t fmt = P.kind_bf16 ? 1u : 2u;
@@ -445,13 +506,12 @@ cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const Gat
   P.acc = reinterpret_cast<double2*>(acc);
   P.err = err;
   const long long grid = std::min<long long>(P.total_tiles, std::max(1, sm_count));
-  const size_t smem = tr_smem_bytes(ns, batch);
-  if (K <= 8)
+  const size_t smem = size_t(P.stages) * 2 * P.atoms * TR_ATOM_BYTES + tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0) +
+                      1024;
+  if (ch == 8)
     cgemm_tc_rows_kernel<8><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
-  else if (K <= 16)
-    cgemm_tc_rows_kernel<16><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   else
-    cgemm_tc_rows_kernel<32><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+    cgemm_tc_rows_kernel<16><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -373,7 +373,7 @@ cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const
                                      int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
                                      int slice_id, cudaStream_t st) {
   if (ns < 1 || ns > RW_SMAX || K > 32 || gd.nrow > 32 || gd.nk > 5) return cudaErrorInvalidConfiguration;
-  const int rows = K <= 16 ? 2 : 1;  // rows per thread
+  const int rows = K <= 8 ? 2 : 1;  // rows per thread (more would cut occupancy)
   const long long tg = (ng + 256 * rows - 1) / (256 * rows);
   if (tg * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const dim3 g2{unsigned(tg * batch), 1u, 1u};
@@ -385,7 +385,7 @@ cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const
     cgemm_rows_gather_kernel<8, 2><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
                                                        g_stride_out, int(tg), slice_id);
   else if (K <= 16)
-    cgemm_rows_gather_kernel<16, 2><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
+    cgemm_rows_gather_kernel<16, 1><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
                                                         g_stride_out, int(tg), slice_id);
   else
     cgemm_rows_gather_kernel<32, 1><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
@@ -399,7 +399,7 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
   if (ns < 1 || ns > RW_SMAX || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
   if (K <= 32 && splits == 1) {
     // short rows: register-resident rows of the large operand
-    const int rows = K <= 16 ? 2 : 1;
+    const int rows = K <= 8 ? 2 : 1;
     const long long tg = (ng + 256 * rows - 1) / (256 * rows);
     if (tg * batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const dim3 g2{unsigned(tg * batch), 1u, 1u};
@@ -410,7 +410,7 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
     if (K <= 8)
       cgemm_rows_regk_kernel<8, 2><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
     else if (K <= 16)
-      cgemm_rows_regk_kernel<16, 2><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
+      cgemm_rows_regk_kernel<16, 1><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
     else
       cgemm_rows_regk_kernel<32, 1><<<g2, 256, 0, st>>>(Sp, Gp, Cp, Ap, ns, ng, K, batch, s_stride_out, g_stride_out, int(tg));
     return cudaGetLastError();

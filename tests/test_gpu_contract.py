@@ -48,7 +48,8 @@ def rel(a, b):
 @pytest.mark.parametrize("mnk", [(2, 3, 4), (6, 6, 6), (7, 5, 8), (3, 9, 10), (8, 8, 2), (6, 8, 10),
                                  (2, 2, 18), (0, 1, 16), (5, 6, 14), (9, 4, 12), (3, 3, 14), (3, 2, 12),
                                  (4, 10, 5), (2, 12, 0), (12, 3, 3), (5, 12, 5), (12, 5, 4), (1, 13, 3),
-                                 (3, 18, 3), (17, 4, 4), (5, 16, 5), (0, 15, 2)])
+                                 (3, 18, 3), (17, 4, 4), (5, 16, 5), (0, 15, 2), (6, 14, 6), (15, 6, 5),
+                                 (6, 13, 3)])
 def test_full_output(T, prec, mnk):
     m, n, k = mnk
     al, bl, ol, A, B = microbench_case(m, n, k, seed=m * 100 + n * 10 + k)
