@@ -26,7 +26,8 @@
 //               the CTA's tiles i = g, g + 2, ...: each thread owns one tile
 //               row and walks it in chunks of up to 16 complex values (loads
 //               of 16-byte pairs when the lowest stored bit is a K bit),
-//               splitting and storing one chunk while the next is in flight;
+//               splitting and storing one chunk while the loads of the next
+//               two (16-value chunks) or four (8-value chunks) are in flight;
 //   warp 8      allocates TMEM and (one thread) issues the MMAs of each tile
 //               into one of the TMEM accumulator buffers;
 //   warps 9-12  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, 32
@@ -215,7 +216,7 @@ __device__ __forceinline__ void load_chunk(const TrParams& P, const uint32_t* ko
   }
 }
 
-template <int CH>
+template <int CH, int DEPTH>
 __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __grid_constant__ TrParams P) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[TR_MAX_STAGES];
@@ -280,31 +281,38 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       const uint32_t h = t / tph, g0 = (t - h * tph) * 128u;
       return lo | deposit(((long long)h * P.ng + g0) >> 7, P.gd.rowpos + 7, nhi);
     };
-    // items (tile, chunk c) in order; the next item's loads are issued before
-    // the current one is split and stored.  Tile i of this CTA (global tile
+    // items (tile, chunk c) in order: the loads of the next DEPTH items are in
+    // flight while one is split and stored.  Tile i of this CTA (global tile
     // blockIdx.x + i * gridDim.x) uses stage i % stages, phase (i / stages) & 1.
-    float2 cur[CH], nxt[CH];
-    uint32_t t = blockIdx.x + uint32_t(grp) * gridDim.x;
+    const uint32_t t0 = blockIdx.x + uint32_t(grp) * gridDim.x;
+    uint32_t tl = t0;  // load cursor
+    int cl = 0;
+    size_t bl = tl < total ? row_base(tl) : 0;
+    auto advance_load = [&]() {
+      if (++cl == nch) {
+        cl = 0;
+        tl += stride2;
+        bl = tl < total ? row_base(tl) : 0;
+      }
+    };
+    float2 buf[DEPTH + 1][CH];
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) {
+      if (tl < total) load_chunk<CH>(P, koff, bl, cl, buf[d]);
+      advance_load();
+    }
+    uint32_t t = t0;  // convert cursor
     int s = grp, c = 0;
     uint32_t ph = 0;
-    size_t base = t < total ? row_base(t) : 0;
-    if (t < total) load_chunk<CH>(P, koff, base, 0, cur);
     while (t < total) {
-      uint32_t t2 = t;
-      int c2 = c + 1;
-      size_t base2 = base;
-      if (c2 == nch) {
-        c2 = 0;
-        t2 = t + stride2;
-        base2 = t2 < total ? row_base(t2) : 0;
-      }
-      if (t2 < total) load_chunk<CH>(P, koff, base2, c2, nxt);
+      if (tl < total) load_chunk<CH>(P, koff, bl, cl, buf[DEPTH]);
+      advance_load();
       if (c == 0 && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
         atomicOr(P.err, 1);
         break;
       }
       uint8_t* st = smem + size_t(s) * stage_bytes;
-      store_chunk<CH>(st, st + stage_bytes / 2, r, cur, c, units, P.kind_bf16, P.split);
+      store_chunk<CH>(st, st + stage_bytes / 2, r, buf[0], c, units, P.kind_bf16, P.split);
       if (c == nch - 1) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&full_bar[s]));
@@ -315,10 +323,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
         }
       }
 #pragma unroll
-      for (int j = 0; j < CH; ++j) cur[j] = nxt[j];
-      t = t2;
-      c = c2;
-      base = base2;
+      for (int d = 0; d < DEPTH; ++d)
+#pragma unroll
+        for (int j = 0; j < CH; ++j) buf[d][j] = buf[d + 1][j];
+      if (++c == nch) {
+        c = 0;
+        t += stride2;
+      }
     }
   } else if (warp == TR_MMA_WARP) {
     if (lane == 0) {
@@ -450,9 +461,9 @@ cudaError_t tc_rows_prepare() {
   static cudaError_t result = cudaErrorUnknown;
   static std::once_flag once;
   std::call_once(once, [] {
-    result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TR_SMEM_MAX));
+    result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TR_SMEM_MAX));
     if (result == cudaSuccess)
-      result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     int(TR_SMEM_MAX));
   });
   return result;
@@ -509,9 +520,9 @@ cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const Gat
   const size_t smem = size_t(P.stages) * 2 * P.atoms * TR_ATOM_BYTES + tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0) +
                       1024;
   if (ch == 8)
-    cgemm_tc_rows_kernel<8><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+    cgemm_tc_rows_kernel<8, 4><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   else
-    cgemm_tc_rows_kernel<16><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+    cgemm_tc_rows_kernel<16, 2><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
 
