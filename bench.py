@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3"])
     ap.add_argument("--batch-log2", type=int, default=2)
-    ap.add_argument("--candidates", type=int, default=512)
+    ap.add_argument("--candidates", type=int, default=2048)
     ap.add_argument("--cap", type=int, default=28)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

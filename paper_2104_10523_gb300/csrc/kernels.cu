@@ -291,9 +291,17 @@ __device__ __forceinline__ void write_pair(const PermDesc& d, void* dst0, void* 
 
 constexpr int PV_THREADS = 256;
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gsrc)
+               : "memory");
+}
+
+// Tiles are double-buffered: the 16-byte loads of the CTA's next tile land in
+// shared memory (cp.async) while the current tile is written out.
 __global__ void __launch_bounds__(PV_THREADS) permute_vec_kernel(const PermDesc d, const float2* __restrict__ src,
                                                                  void* dst0, void* dst1, int slice_id) {
-  __shared__ __align__(16) float2 tile[2048];
+  __shared__ __align__(16) float2 tile[2][2048];
   __shared__ uint32_t srcoff[1024];   // per source-order pair
   __shared__ uint32_t dstoff[1024];   // per destination-order pair
   __shared__ uint16_t epos[2048];     // per destination-order element: swizzled tile position
@@ -320,24 +328,34 @@ __global__ void __launch_bounds__(PV_THREADS) permute_vec_kernel(const PermDesc 
     if (d.slice_src[j] >= 0 && ((slice_id >> j) & 1)) slice_off |= size_t(1) << d.slice_src[j];
   __syncthreads();
   const size_t n_outer = size_t(1) << d.n_outer;
-  for (size_t c = blockIdx.x; c < n_outer; c += gridDim.x) {
-    size_t sb = slice_off, db = 0;
+  auto outer = [&](size_t c, const int* pos) {
+    size_t o = 0;
     for (int k = 0; k < d.n_outer; ++k)
-      if ((c >> k) & 1) {
-        sb |= size_t(1) << d.outer_src[k];
-        db |= size_t(1) << d.outer_dst[k];
-      }
-    for (int q = threadIdx.x; q < P; q += blockDim.x) {
-      const float4 v = *reinterpret_cast<const float4*>(src + sb + srcoff[q]);
-      *reinterpret_cast<float4*>(tile + swz(uint32_t(q) << 1)) = v;
-    }
+      if ((c >> k) & 1) o |= size_t(1) << pos[k];
+    return o;
+  };
+  auto issue = [&](size_t c, int b) {
+    const size_t sb = slice_off | outer(c, d.outer_src);
+    for (int q = threadIdx.x; q < P; q += blockDim.x) cp_async16(&tile[b][swz(uint32_t(q) << 1)], src + sb + srcoff[q]);
+  };
+  int b = 0;
+  if (size_t(blockIdx.x) < n_outer) issue(blockIdx.x, 0);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (size_t c = blockIdx.x; c < n_outer; c += gridDim.x) {
+    const size_t cn = c + gridDim.x;
+    if (cn < n_outer) issue(cn, b ^ 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // tile c has landed (this thread's part)
     __syncthreads();
+    const size_t db = outer(c, d.outer_dst);
     for (int q = threadIdx.x; q < P; q += blockDim.x) {
       const int f = q << 1;
-      write_pair(d, dst0, dst1, db + dstoff[q], tile[epos[f]], tile[epos[f + 1]]);
+      write_pair(d, dst0, dst1, db + dstoff[q], tile[b][epos[f]], tile[b][epos[f + 1]]);
     }
-    __syncthreads();
+    __syncthreads();  // buffer b is refilled by the next iteration's issue
+    b ^= 1;
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 bool perm_vec_ok(const PermDesc& d) {
@@ -352,7 +370,15 @@ cudaError_t launch_permute(const PermDesc& d, const void* src, void* dst0, void*
                            int sm_count, cudaStream_t st) {
   size_t n_outer = size_t(1) << d.n_outer;
   if (perm_vec_ok(d)) {
-    size_t grid = std::min<size_t>(n_outer, size_t(sm_count) * 8);
+    // persistent CTAs: as many as are resident at once
+    static int per_sm = 0;
+    if (per_sm == 0) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, permute_vec_kernel, PV_THREADS, 0) != cudaSuccess || n < 1)
+        n = 4;
+      per_sm = n;
+    }
+    size_t grid = std::min<size_t>(n_outer, size_t(sm_count) * per_sm);
     permute_vec_kernel<<<(unsigned)grid, PV_THREADS, 0, st>>>(d, reinterpret_cast<const float2*>(src), dst0, dst1,
                                                              slice_id);
     return cudaGetLastError();
