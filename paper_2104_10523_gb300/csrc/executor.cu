@@ -136,7 +136,7 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
   // split and multiplied on the tensor cores in one kernel (choice 2, and the
   // default where the shape qualifies).
   const int n_small = std::min(nM, nN), n_big = std::max(nM, nN);
-  const bool tc_rows_ok = choice != 0 && choice != 1 && tc_ok && n_small <= 6 && !use_dot(nM, nN, nK) &&
+  const bool tc_rows_ok = choice != 0 && choice != 1 && tc_ok && n_small <= 7 && !use_dot(nM, nN, nK) &&
                           tc_rows_supported(1 << n_small, 1 << n_big, 1 << nK, 1 << nH, n_big + nH, ctx->precision);
   if (tc_rows_ok || (!use_tc && (rows_capable(nM, nN) || use_dot(nM, nN, nK)) && part)) {
     // bandwidth-bound skinny step: complex64 operands in [h][m|n][k] order
@@ -561,7 +561,7 @@ tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda) {
     if (!tc_ok) continue;  // one candidate only
     // candidates: 0 CUDA cores, 1 tensor-core GEMM, 2 tall-skinny tensor-core kernel
     const int n_small = std::min(s.nM, s.nN), n_big = std::max(s.nM, s.nN);
-    const bool rows_ok = n_small <= 6 && !use_dot(s.nM, s.nN, s.nK) &&
+    const bool rows_ok = n_small <= 7 && !use_dot(s.nM, s.nN, s.nK) &&
                          tc_rows_supported(1 << n_small, 1 << n_big, 1 << s.nK, 1 << s.nH, n_big + s.nH,
                                            ctx->precision);
     float best = 0;

@@ -36,7 +36,7 @@ struct GatherDesc;
 
 // Tall-skinny tensor-core GEMM (gemm_tc_rows.cu): out[h][s][g] (strides
 // s_stride_out, g_stride_out; batch stride ns * ng) = sum_k S[h][s][k] G[h][g][k]
-// for a small operand S ([batch][ns][K] complex64, ns <= 64, K <= 64 in BF16x3
+// for a small operand S ([batch][ns][K] complex64, ns <= 128, K <= 64 in BF16x3
 // or 32 in the TF32 modes) and a large one G read in
 // its stored bit order through gd, split into BF16 or TF32 hi/lo parts in
 // shared memory.  Adds into the FP64 acc when non-null, else writes C.

@@ -1,7 +1,7 @@
 // Tall-skinny complex GEMM on the tcgen05 tensor cores, sm_103a.
 //
 // Steps of the contraction sequence (Sec. 3.1) whose one operand is small
-// (ns <= 64 rows) and whose contracted extent is short (K <= 64) but whose
+// (ns <= 128 rows) and whose contracted extent is short (K <= 64) but whose
 // other operand G is large (ng rows, up to 2^24 and more) do 8 * ns real flops
 // per byte of G: too few for a tensor-core tile built the ordinary way (the
 // 2 * ns-row expansion of the small operand would fill part of a 128-row MMA
@@ -19,7 +19,10 @@
 // straight into the 128-byte-swizzled K-major layout the MMA reads (one or two
 // 128-byte swizzle atoms per row).  The output is written once.  Per 128-row
 // tile: 128 * K * 8 bytes in, 128 * ns * 8 bytes out, 3 * ceil(2K / k_step)
-// MMAs of 128 x Npad (Npad = max(16, 2 ns)).
+// MMAs of 128 x Npad (Npad = max(16, 2 ns) <= 256; four TMEM accumulator
+// buffers for Npad <= 64, two above, at most all 512 columns).  When the
+// expanded small operand of every batch entry does not fit in shared memory,
+// each batch entry gets its own launch.
 //
 // CTA (persistent, one per SM) = 13 warps:
 //   warps 0-7   converters, two groups of four; group g fills the stages of
@@ -472,19 +475,18 @@ cudaError_t tc_rows_prepare() {
 bool tc_rows_supported(int ns, int ng, int K, int batch, int nrow, int precision) {
   if (precision != TNQ_PREC_TF32 && precision != TNQ_PREC_TF32X3 && precision != TNQ_PREC_BF16X3) return false;
   const bool bf16 = precision == TNQ_PREC_BF16X3;
-  // rows of 2K reals span at most two swizzle atoms
-  if (ns < 1 || ns > 64 || K < 1 || K > (bf16 ? 64 : 32) || ng < 128 || (ng & 127) || batch < 1 || nrow < 7)
+  // rows of 2K reals span at most two swizzle atoms; MMA N = 2 ns <= 256
+  if (ns < 1 || ns > 128 || K < 1 || K > (bf16 ? 64 : 32) || ng < 128 || (ng & 127) || batch < 1 || nrow < 7)
     return false;
-  return tr_bprime_bytes(ns, K, batch, bf16) <= size_t(TR_BPRIME_BUDGET);
+  // S' of one batch entry must fit (larger batches run one launch per entry)
+  return tr_bprime_bytes(ns, K, 1, bf16) <= size_t(TR_BPRIME_BUDGET);
 }
 
-cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
-                                 int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
-                                 int precision, int* err, int sm_count, cudaStream_t st) {
-  if (!tc_rows_supported(ns, ng, K, batch, gd.nrow, precision) || !err) return cudaErrorNotSupported;
-  if (gd.nk > 6 || gd.nrow > 32 || (1 << gd.nk) != K) return cudaErrorInvalidValue;
-  cudaError_t pe = tc_rows_prepare();
-  if (pe != cudaSuccess) return pe;
+namespace {
+
+cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
+                               int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
+                               int precision, int* err, int sm_count, cudaStream_t st) {
   TrParams P;
   P.S = reinterpret_cast<const float2*>(Ssmall);
   P.G = reinterpret_cast<const float2*>(Gsrc);
@@ -500,7 +502,7 @@ cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const Gat
   P.nks = (K + k_step - 1) / k_step;
   P.atoms = tr_atoms(K, P.kind_bf16 != 0);
   P.stages = P.atoms == 1 ? 4 : 2;
-  P.nacc = P.npad <= 64 ? 4 : 2;
+  P.nacc = P.npad <= 64 ? 4 : 2;  // TMEM: npad * nacc <= 512 columns
   const int ch = K <= 8 ? 8 : 16;
   P.nchunks = (K + ch - 1) / ch;
   P.pairs = gd.nk >= 1 && gd.kpos[0] == 0;
@@ -524,6 +526,42 @@ cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const Gat
   else
     cgemm_tc_rows_kernel<16, 2><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
+                                 int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
+                                 int precision, int* err, int sm_count, cudaStream_t st) {
+  if (!tc_rows_supported(ns, ng, K, batch, gd.nrow, precision) || !err) return cudaErrorNotSupported;
+  if (gd.nk > 6 || gd.nrow > 32 || (1 << gd.nk) != K) return cudaErrorInvalidValue;
+  cudaError_t pe = tc_rows_prepare();
+  if (pe != cudaSuccess) return pe;
+  const bool bf16 = precision == TNQ_PREC_BF16X3;
+  if (tr_bprime_bytes(ns, K, batch, bf16) <= size_t(TR_BPRIME_BUDGET))
+    return launch_tc_rows_one(Ssmall, Gsrc, gd, C, acc, ns, ng, K, batch, s_stride_out, g_stride_out, slice_id,
+                              precision, err, sm_count, st);
+  // S' of every batch entry does not fit: one launch per entry, whose batch
+  // bits (the row bits above the ng bits) become extra slice bits of G
+  int gbits = 0;
+  while ((1 << gbits) < ng) ++gbits;
+  const int hbits = gd.nrow - gbits;
+  if (hbits < 0 || (1 << hbits) != batch || gd.n_slice + hbits > 30) return cudaErrorNotSupported;
+  GatherDesc g1 = gd;
+  g1.nrow = gbits;
+  for (int j = 0; j < hbits; ++j) g1.slice_src[gd.n_slice + j] = gd.rowpos[gbits + j];
+  g1.n_slice = gd.n_slice + hbits;
+  const float2* S = reinterpret_cast<const float2*>(Ssmall);
+  for (int h = 0; h < batch; ++h) {
+    const size_t ob = size_t(h) * ns * ng;
+    cudaError_t e = launch_tc_rows_one(S + size_t(h) * ns * K, Gsrc, g1,
+                                       C ? static_cast<void*>(reinterpret_cast<float2*>(C) + ob) : nullptr,
+                                       acc ? static_cast<void*>(reinterpret_cast<double2*>(acc) + ob) : nullptr, ns,
+                                       ng, K, 1, s_stride_out, g_stride_out, slice_id | (h << gd.n_slice), precision,
+                                       err, sm_count, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace tnq

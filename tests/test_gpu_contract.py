@@ -49,7 +49,7 @@ def rel(a, b):
                                  (2, 2, 18), (0, 1, 16), (5, 6, 14), (9, 4, 12), (3, 3, 14), (3, 2, 12),
                                  (4, 10, 5), (2, 12, 0), (12, 3, 3), (5, 12, 5), (12, 5, 4), (1, 13, 3),
                                  (3, 18, 3), (17, 4, 4), (5, 16, 5), (0, 15, 2), (6, 14, 6), (15, 6, 5),
-                                 (6, 13, 3)])
+                                 (6, 13, 3), (7, 14, 4), (13, 7, 5)])
 def test_full_output(T, prec, mnk):
     m, n, k = mnk
     al, bl, ol, A, B = microbench_case(m, n, k, seed=m * 100 + n * 10 + k)
@@ -86,17 +86,21 @@ def test_batch_labels(T, prec):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16x3"])
-def test_tall_skinny_batch(T, prec):
-    """A tall-skinny step with batch labels (2^3 x 2^14 output per batch entry,
-    K = 2^3, 2^2 batch entries, every operand's bits scattered): the large
-    operand is gathered in place and the small one expanded per batch entry."""
-    rng = np.random.default_rng(11)
-    small, big, kl, hl = [10, 11, 12], list(range(20, 34)), [0, 1, 2], [100, 101]
+@pytest.mark.parametrize("shape", [(3, 14, 3), (7, 12, 5)])
+def test_tall_skinny_batch(T, prec, shape):
+    """A tall-skinny step with batch labels (2^s x 2^g output per batch entry,
+    K = 2^k, 2^2 batch entries, every operand's bits scattered): the large
+    operand is gathered in place and the small one expanded per batch entry
+    (with 2^7 small rows, one launch per batch entry)."""
+    ns, ng, nk = shape
+    rng = np.random.default_rng(11 + ns)
+    small, big = list(range(40, 40 + ns)), list(range(60, 60 + ng))
+    kl, hl = list(range(nk)), [100, 101]
     al = list(rng.permutation(small + kl + hl))
     bl = list(rng.permutation(big + kl + hl))
     ol = list(rng.permutation(small + big + hl))
-    A = (rng.standard_normal(2 ** 8) + 1j * rng.standard_normal(2 ** 8)).astype(np.complex64)
-    B = (rng.standard_normal(2 ** 19) + 1j * rng.standard_normal(2 ** 19)).astype(np.complex64)
+    A = (rng.standard_normal(2 ** len(al)) + 1j * rng.standard_normal(2 ** len(al))).astype(np.complex64)
+    B = (rng.standard_normal(2 ** len(bl)) + 1j * rng.standard_normal(2 ** len(bl))).astype(np.complex64)
     C = _run(T, prec, A, al, B, bl, ol)
     ref = contraction.contract_labeled(A, al, B, bl, ol)
     assert np.all(np.isfinite(C))
