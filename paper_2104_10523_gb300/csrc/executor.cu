@@ -144,12 +144,45 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
     // instead of being permuted first.
     const bool small_is_a = nM <= nN;
     const bool gather = tc_rows_ok || (!use_dot(nM, nN, nK) && nK <= 5 && (small_is_a ? perm_b : perm_a));
-    if (perm_a && !(gather && !small_is_a)) {
+    // Dot steps read an operand in place when its stored layout starts with at
+    // least 2^5 K values in the required K order (one contiguous run) and keeps
+    // every K bit above the run in K order too (the kernel steps its K offset
+    // by adding in the deposited domain, which needs increasing positions).
+    auto inplace_dot = [&](const void* src, const std::vector<int>& st, const std::vector<int>& req, DotOp* d) {
+      if (!use_dot(nM, nN, nK) || nK > 40 || (int)req.size() - nK > 24) return false;
+      auto spos = [&](int l) { return int(std::find(st.begin(), st.end(), l) - st.begin()); };
+      *d = DotOp{};
+      d->nk = nK;
+      d->kmask = 0;
+      for (int j = 0; j < nK; ++j) {
+        const int q = spos(req[j]);
+        if (q >= (int)st.size() || (j < 5 && q != j) || (j > 0 && q <= d->kpos[j - 1])) return false;
+        d->kpos[j] = (signed char)q;
+        d->kmask |= 1ull << q;
+      }
+      d->nrow = (int)req.size() - nK;
+      for (int j = 0; j < d->nrow; ++j) {
+        const int q = spos(req[nK + j]);
+        if (q >= (int)st.size()) return false;
+        d->rowpos[j] = (signed char)q;
+      }
+      size_t soff = 0;
+      for (int j = 0; j < ns; ++j) {
+        const int q = spos(slice_labels[j]);
+        if (q < (int)st.size() && ((slice_id >> j) & 1)) soff |= size_t(1) << q;
+      }
+      d->p = reinterpret_cast<const float2*>(src) + soff;
+      return true;
+    };
+    DotOp dot_a, dot_b;
+    const bool inpl_a = perm_a && inplace_dot(a_src, a_labels, a_req, &dot_a);
+    const bool inpl_b = perm_b && inplace_dot(b_src, b_labels, b_req, &dot_b);
+    if (perm_a && !inpl_a && !(gather && !small_is_a)) {
       build_perm_desc(a_labels.data(), (int)a_labels.size(), a_req.data(), (int)a_req.size(), slice_labels.data(),
                       ns, PM_C64, nK, &d);
       TNQ_CUDA(perm(ctx, d, a_src, scratch_a, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)a_req.size())));
     }
-    if (perm_b && !(gather && small_is_a)) {
+    if (perm_b && !inpl_b && !(gather && small_is_a)) {
       build_perm_desc(b_labels.data(), (int)b_labels.size(), b_req.data(), (int)b_req.size(), slice_labels.data(),
                       ns, PM_C64, nK, &d);
       TNQ_CUDA(perm(ctx, d, b_src, scratch_b, nullptr, slice_id, 16.0 * std::ldexp(1.0, (int)b_req.size())));
@@ -203,7 +236,9 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
     int splits;
     if (use_dot(nM, nN, nK)) {
       splits = dot_splits(nH, nM, nN, nK);
-      e = launch_cdot(A, B, part, splits, M, N, K, H, ctx->stream);
+      if (!inpl_a) dot_a = dot_contiguous(A, M, K, H);
+      if (!inpl_b) dot_b = dot_contiguous(B, N, K, H);
+      e = launch_cdot_ops(dot_a, dot_b, part, splits, M, N, K, H, ctx->stream);
       if (e == cudaSuccess) e = launch_reduce_splits(part, splits, out_elems, C, acc, ctx->sm_count, ctx->stream);
     } else {
       splits = rows_splits(nH, nM, nN, nK);

@@ -57,6 +57,20 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
                               cudaStream_t st);
 cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, int M, int N, int K, int batch,
                         cudaStream_t st);
+// Operand of the dot kernel addressed through bit deposits: element (row r of
+// batch entry h, k) sits at p + dep(h * rows + r, rowpos) + dep(k, kpos), with
+// kmask = OR of 1 << kpos[j].  kpos[0] must be 0 (16-byte pair loads) and
+// kpos must increase.
+struct DotOp {
+  const float2* p;              // slice offset already added
+  unsigned long long kmask;
+  int nk, nrow;
+  signed char kpos[40];
+  signed char rowpos[24];
+};
+DotOp dot_contiguous(const void* p, int rows, int K, int batch);
+cudaError_t launch_cdot_ops(const DotOp& A, const DotOp& B, void* part, int splits, int M, int N, int K, int batch,
+                            cudaStream_t st);
 
 // Bit positions (in the large operand's stored layout) of its row index (the
 // N or M bits, then the batch bits) and of its K bits, plus sliced labels.

@@ -68,10 +68,32 @@ void layout_steps(Plan* p) {
     bool x_is_a = lx.size() <= ly.size();
     int a = x_is_a ? x : y, b = x_is_a ? y : x;
     std::vector<int> la = x_is_a ? lx : ly, lb = x_is_a ? ly : lx;
-    const std::vector<int>& anchor = lb;  // K and H orders follow the larger operand
+    // K and H orders follow the larger operand, except in dot-shaped steps
+    // (at most 8 x 8 outputs per batch entry, at least 2^10 K values): there they
+    // follow the operand whose stored layout starts with the longer run of K
+    // labels, which the dot kernel then reads in place
+    int nk_all = 0, nm = 0, nn = 0;
+    for (int l : lb)
+      if (contains(la, l) && !contains(out_set, l)) ++nk_all;
+    for (int l : la)
+      if (!contains(lb, l)) ++nm;
+    for (int l : lb)
+      if (!contains(la, l)) ++nn;
+    auto low_k_run = [&](int id) {
+      int run = 0;
+      for (int l : p->tensors[id].labels) {
+        if (p->sliced[l] || !contains(la, l) || !contains(lb, l) || contains(out_set, l)) break;
+        ++run;
+      }
+      return run;
+    };
+    const bool dot_shaped = nm <= 3 && nn <= 3 && nk_all >= 10;
+    const bool anchor_a = dot_shaped && low_k_run(a) > low_k_run(b);
+    const std::vector<int>& anchor = anchor_a ? la : lb;
+    const std::vector<int>& other = anchor_a ? lb : la;
     std::vector<int> K, Hh, M, N;
     for (int l : anchor)
-      if (contains(la, l)) (contains(out_set, l) ? Hh : K).push_back(l);
+      if (contains(other, l)) (contains(out_set, l) ? Hh : K).push_back(l);
     for (int l : la)
       if (!contains(lb, l)) M.push_back(l);
     for (int l : lb)

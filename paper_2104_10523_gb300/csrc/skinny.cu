@@ -104,21 +104,30 @@ constexpr int DOT_THREADS = 256;
 // read it in the same 16-byte load instruction and every loaded value serves
 // TN (or TM) complex multiply-adds from registers.  Each thread keeps two
 // K-pairs in flight per iteration; per-CTA partials go to part[split][batch][M][N].
-template <int TM, int TN>
-__device__ __forceinline__ void cdot_load(const float2* __restrict__ Ar, const float2* __restrict__ Br, int K, int k,
-                                          int kend, float4 (&a)[TM], float4 (&b)[TN]) {
-  const bool in = k < kend, two = k + 1 < kend;
+//
+// Each operand is addressed as row base + K offset, both bit deposits of the
+// row index (row bits, then batch bits) and of k into the operand's stored bit
+// positions (DotOp): a contiguous [batch][rows][K] operand has K in the low
+// bits; an operand read in place (its permute fused) has them where it stores
+// them, in increasing positions.  A thread advances its K offset by adding in
+// the deposited domain: dep(k + d) = ((dep(k) | ~mask) + dep(d)) & mask, the
+// carries running through the non-K positions.
+__device__ __forceinline__ size_t dot_dep(long long v, const signed char* pos, int n) {
+  size_t o = 0;
+  for (int j = 0; j < n; ++j)
+    if ((v >> j) & 1) o |= size_t(1) << pos[j];
+  return o;
+}
+
+__device__ __forceinline__ size_t dep_add(size_t x, size_t inc, size_t mask) { return ((x | ~mask) + inc) & mask; }
+
+template <int R>
+__device__ __forceinline__ void cdot_load(const float2* __restrict__ p, const size_t (&row)[R], size_t koff, bool in,
+                                          float4 (&v)[R]) {
 #pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (two) a[i] = *reinterpret_cast<const float4*>(Ar + size_t(i) * K + k);
-    else if (in) { const float2 v = Ar[size_t(i) * K + k]; a[i].x = v.x; a[i].y = v.y; }
-  }
-#pragma unroll
-  for (int j = 0; j < TN; ++j) {
-    b[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (two) b[j] = *reinterpret_cast<const float4*>(Br + size_t(j) * K + k);
-    else if (in) { const float2 v = Br[size_t(j) * K + k]; b[j].x = v.x; b[j].y = v.y; }
+  for (int i = 0; i < R; ++i) {
+    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (in) v[i] = *reinterpret_cast<const float4*>(p + row[i] + koff);
   }
 }
 
@@ -141,8 +150,8 @@ __device__ __forceinline__ void cdot_fma(const float4 (&a)[TM], const float4 (&b
 }
 
 template <int TM, int TN>
-__global__ void __launch_bounds__(DOT_THREADS, 2) cdot_blk_kernel(const float2* __restrict__ A,
-                                                                  const float2* __restrict__ B,
+__global__ void __launch_bounds__(DOT_THREADS, 2) cdot_blk_kernel(const __grid_constant__ DotOp A,
+                                                                  const __grid_constant__ DotOp B,
                                                                   float2* __restrict__ part, int M, int N, int K,
                                                                   int kchunk) {
   __shared__ float red[DOT_THREADS / 32][2 * 64];
@@ -152,20 +161,34 @@ __global__ void __launch_bounds__(DOT_THREADS, 2) cdot_blk_kernel(const float2* 
   const int blk = threadIdx.x & (nb - 1), kq = threadIdx.x / nb;
   const int bi = blk / nbj, bj = blk % nbj;
   const int step = 2 * (DOT_THREADS / nb);  // K values one CTA iteration covers
-  const float2* Ar = A + size_t(h) * M * K + size_t(bi * TM) * K;
-  const float2* Br = B + size_t(h) * N * K + size_t(bj * TN) * K;
+  size_t ra[TM], rb[TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) ra[i] = dot_dep((long long)h * M + bi * TM + i, A.rowpos, A.nrow);
+#pragma unroll
+  for (int j = 0; j < TN; ++j) rb[j] = dot_dep((long long)h * N + bj * TN + j, B.rowpos, B.nrow);
+  const size_t ma = A.kmask, mb = B.kmask;
+  const size_t a_step = dot_dep(step, A.kpos, A.nk), b_step = dot_dep(step, B.kpos, B.nk);
+  const size_t a_2step = dot_dep(2 * step, A.kpos, A.nk), b_2step = dot_dep(2 * step, B.kpos, B.nk);
   float cr[TM][TN], ci[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0.f;
-  // kbeg is even (kchunk is), so every 16-byte load is aligned when K is even
-  for (int k = kbeg + 2 * kq; k < kend; k += 2 * step) {
+  // k is even and K bit 0 is stored bit 0 of both operands, so (k, k+1) is one
+  // aligned 16-byte pair; kend is even
+  int k = kbeg + 2 * kq;
+  size_t ka = dot_dep(k, A.kpos, A.nk), kb = dot_dep(k, B.kpos, B.nk);
+  for (; k < kend; k += 2 * step) {
     float4 a0[TM], b0[TN], a1[TM], b1[TN];
-    cdot_load<TM, TN>(Ar, Br, K, k, kend, a0, b0);
-    cdot_load<TM, TN>(Ar, Br, K, k + step, kend, a1, b1);
+    const bool in1 = k + step < kend;
+    cdot_load<TM>(A.p, ra, ka, true, a0);
+    cdot_load<TN>(B.p, rb, kb, true, b0);
+    cdot_load<TM>(A.p, ra, dep_add(ka, a_step, ma), in1, a1);
+    cdot_load<TN>(B.p, rb, dep_add(kb, b_step, mb), in1, b1);
     cdot_fma<TM, TN>(a0, b0, cr, ci);
     cdot_fma<TM, TN>(a1, b1, cr, ci);
+    ka = dep_add(ka, a_2step, ma);
+    kb = dep_add(kb, b_2step, mb);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -426,25 +449,53 @@ cudaError_t launch_cgemm_rows(const void* Ssmall, const void* Gbig, void* C, voi
   return cudaGetLastError();
 }
 
-cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, int M, int N, int K, int batch,
-                        cudaStream_t st) {
+DotOp dot_contiguous(const void* p, int rows, int K, int batch) {
+  // [batch][rows][K]: K bits lowest, then the row bits, then the batch bits
+  DotOp d{};
+  d.p = reinterpret_cast<const float2*>(p);
+  int nk = 0, nr = 0, nh = 0;
+  while ((1 << nk) < K) ++nk;
+  while ((1 << nr) < rows) ++nr;
+  while ((1 << nh) < batch) ++nh;
+  d.nk = nk;
+  for (int j = 0; j < nk; ++j) d.kpos[j] = (signed char)j;
+  d.nrow = nr + nh;
+  for (int j = 0; j < nr + nh; ++j) d.rowpos[j] = (signed char)(nk + j);
+  d.kmask = (nk >= 64) ? ~0ull : ((1ull << nk) - 1);
+  return d;
+}
+
+cudaError_t launch_cdot_ops(const DotOp& A, const DotOp& B, void* part, int splits, int M, int N, int K, int batch,
+                            cudaStream_t st) {
   if (M < 1 || M > 8 || N < 1 || N > 8 || splits < 1 || batch > 65535) return cudaErrorInvalidConfiguration;
+  // M, N and K are powers of two (all-dim-2 tensors); K bit 0 must be stored
+  // bit 0 of both operands for the 16-byte pair loads
+  if ((M & (M - 1)) || (N & (N - 1)) || (K & (K - 1)) || K < 2) return cudaErrorInvalidConfiguration;
+  if (A.nk < 1 || B.nk < 1 || A.kpos[0] != 0 || B.kpos[0] != 0 || A.nk > 40 || B.nk > 40 || A.nrow > 24 ||
+      B.nrow > 24)
+    return cudaErrorInvalidConfiguration;
+  // K offsets advance by carry-through-mask addition: positions must increase
+  for (int j = 1; j < A.nk; ++j)
+    if (A.kpos[j] <= A.kpos[j - 1]) return cudaErrorInvalidConfiguration;
+  for (int j = 1; j < B.nk; ++j)
+    if (B.kpos[j] <= B.kpos[j - 1]) return cudaErrorInvalidConfiguration;
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + 1) & ~1;
   dim3 grid{unsigned(splits), unsigned(batch), 1u};
-  const float2* Ap = reinterpret_cast<const float2*>(A);
-  const float2* Bp = reinterpret_cast<const float2*>(B);
   float2* Pp = reinterpret_cast<float2*>(part);
-  // M and N are powers of two (all-dim-2 tensors); K even keeps the 16-byte
-  // loads of every row aligned
-  if ((M & (M - 1)) || (N & (N - 1)) || (K & 1)) return cudaErrorInvalidConfiguration;
   const int tm = M < 4 ? M : 4, tn = N < 4 ? N : 4;
 #define TNQ_DOT(TM_, TN_) \
-  if (tm == TM_ && tn == TN_) cdot_blk_kernel<TM_, TN_><<<grid, DOT_THREADS, 0, st>>>(Ap, Bp, Pp, M, N, K, kchunk)
+  if (tm == TM_ && tn == TN_) cdot_blk_kernel<TM_, TN_><<<grid, DOT_THREADS, 0, st>>>(A, B, Pp, M, N, K, kchunk)
   TNQ_DOT(1, 1); else TNQ_DOT(1, 2); else TNQ_DOT(1, 4); else TNQ_DOT(2, 1); else TNQ_DOT(2, 2);
   else TNQ_DOT(2, 4); else TNQ_DOT(4, 1); else TNQ_DOT(4, 2); else TNQ_DOT(4, 4);
 #undef TNQ_DOT
   return cudaGetLastError();
+}
+
+cudaError_t launch_cdot(const void* A, const void* B, void* part, int splits, int M, int N, int K, int batch,
+                        cudaStream_t st) {
+  return launch_cdot_ops(dot_contiguous(A, M, K, batch), dot_contiguous(B, N, K, batch), part, splits, M, N, K, batch,
+                         st);
 }
 
 }  // namespace tnq

@@ -107,6 +107,30 @@ def test_tall_skinny_batch(T, prec, shape):
     assert rel(C, ref) <= TOL[prec], (prec, rel(C, ref))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("both", [False, True])
+def test_dot_in_place(T, prec, both):
+    """A dot-shaped contraction (2^3 x 2^3 outputs, K = 2^14, 2^2 batch
+    entries) whose larger operand stores seven K labels lowest: the dot kernel
+    reads it in place, K ordered by it; with `both` the other operand stores
+    its K labels in the same order (other labels between them) and neither is
+    permuted."""
+    rng = np.random.default_rng(23)
+    kl, ml, nl, hl = list(range(14)), [20, 21, 22], [30, 31, 32], [40, 41]
+    bl = kl[:7] + [30, 40] + kl[7:] + [31, 41, 32]
+    if both:
+        al = kl[:7] + [20, 40] + kl[7:11] + [21] + kl[11:] + [41, 22]
+    else:
+        al = list(rng.permutation(kl + ml + hl))
+    ol = list(rng.permutation(ml + nl + hl))
+    A = (rng.standard_normal(2 ** 19) + 1j * rng.standard_normal(2 ** 19)).astype(np.complex64)
+    B = (rng.standard_normal(2 ** 19) + 1j * rng.standard_normal(2 ** 19)).astype(np.complex64)
+    C = _run(T, prec, A, al, B, bl, ol)
+    ref = contraction.contract_labeled(A, al, B, bl, ol)
+    assert np.all(np.isfinite(C))
+    assert rel(C, ref) <= TOL[prec], (prec, rel(C, ref))
+
+
 def test_invalid_labels_rejected(T):
     import torch
     ctx = T.Context(0, "fp32")
