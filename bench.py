@@ -339,7 +339,7 @@ def roofline_of(rec, precision):
     k = max(tot, key=lambda x: tot[x][0])
     ms, flops, nbytes, n = tot[k]
     bf16_sus = float(peaks.get("bf16_tflops_sustained", 1720.9))
-    traffic = load_traffic(kinds[k])
+    traffic = load_traffic(kinds[k], nbytes / n)
     if k == 2:
         # tensor-pipe peak of the mode: TF32 runs at half the BF16 rate (nominal 1.1 vs 2.25 PF/s);
         # the split modes issue three products per useful product.
@@ -363,9 +363,12 @@ def roofline_of(rec, precision):
              "traffic": traffic, "launches": n, "avg_launch_ms": ms / n, "peak_source": f"{src} copy"}, share)
 
 
-def load_traffic(kernel):
+def load_traffic(kernel, alg_bytes_per_launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source (else None).  The summary holds the measured DRAM
+    bytes over the algorithmic bytes of a captured small case; traffic scales in
+    proportion to the units a launch processes, so that ratio times this
+    workload's algorithmic bytes per launch is the traffic per launch here."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -381,7 +384,9 @@ def load_traffic(kernel):
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+    if h != ent.get("source_sha256_16"):
+        return None
+    return ent["dram_over_algorithmic"] * alg_bytes_per_launch
 
 
 def run_pair(a, local, rank):

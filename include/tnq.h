@@ -100,7 +100,8 @@ typedef struct {
   int max_log2;              /* largest intermediate, log2 elements, after slicing */
   int batch_log2, traj_log2;
   double flops_per_pass;     /* 8 real flops per complex multiply-add, one slice */
-  double flops_per_batch;    /* flops_per_pass * 2^n_sliced */
+  double flops_per_batch;    /* flops executed per batch: steps whose subtree holds
+                                no sliced label run once, the others once per slice */
   double bytes_per_pass;     /* algorithmic HBM bytes of the GEMM and permute steps */
   double search_ms;          /* host time of the path search and slicing */
   size_t workspace_bytes;    /* device bytes tnq_plan_bind needs */
@@ -138,7 +139,9 @@ tnq_status tnq_plan_create(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_
 void tnq_plan_destroy(tnq_plan* p);
 tnq_status tnq_plan_get_info(const tnq_plan* p, tnq_plan_info* info);
 /* Per-step shape record: for step i, writes 8 ints
- * {a_rank, b_rank, out_rank, log2 H, log2 M, log2 N, log2 K, a_is_leaf | b_is_leaf << 1}.
+ * {a_rank, b_rank, out_rank, log2 H, log2 M, log2 N, log2 K,
+ *  a_is_leaf | b_is_leaf << 1 | slice_invariant << 2}, where slice_invariant
+ * marks a step whose subtree holds no sliced label (run once per batch).
  * rec must hold 8 * n_steps ints. */
 tnq_status tnq_plan_get_steps(const tnq_plan* p, int* rec);
 

@@ -169,7 +169,11 @@ tnq_status tnq_plan_get_info(const tnq_plan* pp, tnq_plan_info* info) {
   info->batch_log2 = p.batch_log2;
   info->traj_log2 = p.traj_log2;
   info->flops_per_pass = p.cost.flops;
-  info->flops_per_batch = p.cost.flops * std::ldexp(1.0, (int)p.slice_labels.size());
+  // executed flops: slice-invariant steps once per batch, the rest per slice
+  const double n_slices = std::ldexp(1.0, (int)p.slice_labels.size());
+  double fb = 0;
+  for (const auto& s : p.steps) fb += s.invariant ? s.flops : s.flops * n_slices;
+  info->flops_per_batch = fb;
   info->bytes_per_pass = p.cost.bytes;
   info->search_ms = p.search_ms;
   info->workspace_bytes = p.ws_total;
@@ -190,7 +194,7 @@ tnq_status tnq_plan_get_steps(const tnq_plan* pp, int* rec) {
     r[4] = s.nM;
     r[5] = s.nN;
     r[6] = s.nK;
-    r[7] = (s.a < L ? 1 : 0) | (s.b < L ? 2 : 0);
+    r[7] = (s.a < L ? 1 : 0) | (s.b < L ? 2 : 0) | (s.invariant ? 4 : 0);
   }
   return TNQ_OK;
 }

@@ -136,7 +136,8 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
   // split and multiplied on the tensor cores in one kernel (choice 2, and the
   // default where the shape qualifies).
   const int n_small = std::min(nM, nN), n_big = std::max(nM, nN);
-  const bool tc_rows_ok = choice != 0 && choice != 1 && tc_ok && n_small <= 7 && !use_dot(nM, nN, nK) &&
+  const bool tc_rows_ok = choice != 0 && choice != 1 && ctx->precision != TNQ_PREC_FP32 && n_small <= 7 &&
+                          !use_dot(nM, nN, nK) &&
                           tc_rows_supported(1 << n_small, 1 << n_big, 1 << nK, 1 << nH, n_big + nH, ctx->precision);
   if (tc_rows_ok || (!use_tc && (rows_capable(nM, nN) || use_dot(nM, nN, nK)) && part)) {
     // bandwidth-bound skinny step: complex64 operands in [h][m|n][k] order
@@ -353,9 +354,12 @@ tnq_status run_step(Ctx* ctx, Plan* p, size_t si, int slice_id, char* ws, int ch
                        ws + p->ws_partial, choice);
 }
 
-tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws) {
+// One slice of a batch; slice-invariant steps run only in the batch's first
+// slice (their outputs persist for the batch).
+tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws, bool first) {
   const bool tuned = p->tuned_precision == ctx->precision && p->kernel_choice.size() == p->steps.size();
   for (size_t si = 0; si < p->steps.size(); ++si) {
+    if (p->steps[si].invariant && !first) continue;
     ctx->cur_step = (int)si;
     tnq_status st = run_step(ctx, p, si, slice_id, ws, tuned ? p->kernel_choice[si] : -1);
     if (st != TNQ_OK) return st;
@@ -395,7 +399,7 @@ tnq_status enqueue_batch(Ctx* ctx, Plan* p, int64_t nv, const int* pos) {
   TNQ_CUDA(launch_zero(ws + p->ws_acc, 16 * (size_t(1) << p->tensors[p->root].rank), ctx->stream));
   const int n_slices = 1 << p->slice_labels.size();
   for (int s = 0; s < n_slices; ++s) {
-    tnq_status st = run_pass(ctx, p, s, ws);
+    tnq_status st = run_pass(ctx, p, s, ws, s == 0);
     if (st != TNQ_OK) return st;
   }
   TNQ_CUDA(launch_finalize(ws + p->ws_acc, ws + p->ws_out_stage, nv, pos, w, ctx->stream));
@@ -553,7 +557,7 @@ tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* 
     ctx->launches++;
     TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
     for (int64_t s = slice_begin; s < slice_begin + slice_count; ++s) {
-      tnq_status st = run_pass(ctx, p, int(s), ws);
+      tnq_status st = run_pass(ctx, p, int(s), ws, s == slice_begin);
       if (st != TNQ_OK) return st;
     }
     double* dst = out_dev ? out + 2 * base : out_stage;
@@ -593,15 +597,21 @@ tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda) {
     const bool tc_ok = ctx->precision != TNQ_PREC_FP32 &&
                        tc_gemm_supported(1 << s.nM, 1 << s.nN, 1 << s.nK, ctx->precision) &&
                        s.nM + s.nN + s.nK + s.nH >= 12;
-    if (!tc_ok) continue;  // one candidate only
     // candidates: 0 CUDA cores, 1 tensor-core GEMM, 2 tall-skinny tensor-core kernel
     const int n_small = std::min(s.nM, s.nN), n_big = std::max(s.nM, s.nN);
-    const bool rows_ok = n_small <= 7 && !use_dot(s.nM, s.nN, s.nK) &&
+    const bool rows_ok = ctx->precision != TNQ_PREC_FP32 && n_small <= 7 && !use_dot(s.nM, s.nN, s.nK) &&
+                         s.nM + s.nN + s.nK + s.nH >= 12 &&
                          tc_rows_supported(1 << n_small, 1 << n_big, 1 << s.nK, 1 << s.nH, n_big + s.nH,
                                            ctx->precision);
+    int cands[3], nc = 0;
+    cands[nc++] = 0;
+    if (tc_ok) cands[nc++] = 1;
+    if (rows_ok) cands[nc++] = 2;
+    if (nc == 1) continue;  // one candidate only
     float best = 0;
     int pick = -1;
-    for (int c = 0; c < (rows_ok ? 3 : 2) && result == TNQ_OK; ++c) {
+    for (int ci = 0; ci < nc && result == TNQ_OK; ++ci) {
+      const int c = cands[ci];
       float tmin = 1e30f;
       for (int r = 0; r < reps + 1; ++r) {  // first run warms up
         cudaEventRecord(e0, ctx->stream);
@@ -695,7 +705,7 @@ tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, u
       ctx->launches++;
       TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
       for (int s = 0; s < n_slices; ++s) {
-        st = run_pass(ctx, p, s, ws);
+        st = run_pass(ctx, p, s, ws, s == 0);
         if (st != TNQ_OK) return st;
       }
       st = consume(0, base, nv, tb, nt, bpos, tpos);

@@ -110,6 +110,9 @@ struct Step {
   std::vector<int> a_req, b_req;  // required operand layouts: [K][M|N][H] (bit 0 first)
   std::vector<int> out_labels;    // [N][M][H]
   bool perm_a = false, perm_b = false;
+  // no sliced label in the step's subtree: its result is the same for every
+  // slice, so a batch computes it in its first slice only
+  bool invariant = false;
   double flops = 0;
 };
 
@@ -133,6 +136,9 @@ struct Plan {
   int batch_log2 = 0, traj_log2 = 0;
   int root = -1;
   // workspace layout (bytes)
+  // persist: outputs of slice-invariant steps read by slice-dependent steps
+  // (kept for the whole batch, outside the reusable arena)
+  size_t ws_persist = 0, ws_persist_bytes = 0;
   size_t ws_leaves = 0, ws_arena = 0, ws_arena_bytes = 0, ws_scratch_a = 0, ws_scratch_b = 0, ws_partial = 0,
          ws_scratch_bytes = 0, ws_acc = 0, ws_misc = 0, ws_total = 0;
   // misc region: [flags 256 B][bit staging][output staging 16 B x 2^w][psum][p2sum]

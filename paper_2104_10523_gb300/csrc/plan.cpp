@@ -128,6 +128,23 @@ void layout_steps(Plan* p) {
   }
   p->root = L + (int)t.nodes.size() - 1;
   p->max_operand_log2 = max_op;
+  // slice dependence: a leaf depends on the slice when it holds a sliced label,
+  // a step output when either operand does
+  std::vector<char> dep(p->tensors.size(), 0);
+  for (int i = 0; i < L; ++i)
+    for (int l : p->net.leaves[i].labels)
+      if (p->sliced[l]) dep[i] = 1;
+  for (auto& s : p->steps) {
+    dep[s.out] = dep[s.a] || dep[s.b];
+    s.invariant = !dep[s.out];
+  }
+  // invariant outputs consumed by a slice-dependent step persist for the batch
+  std::vector<char> pinned(p->tensors.size(), 0);
+  for (auto& s : p->steps)
+    if (!s.invariant) {
+      if (s.a >= L && !dep[s.a]) pinned[s.a] = 1;
+      if (s.b >= L && !dep[s.b]) pinned[s.b] = 1;
+    }
 
   // ---- workspace: [leaves][arena of intermediates][scratch A][scratch B][acc][misc]
   size_t off = 0;
@@ -137,6 +154,15 @@ void layout_steps(Plan* p) {
     off += (size_t(8) << p->tensors[i].rank);
   }
   p->ws_leaves = 0;
+  off = align_up(off, 256);
+  p->ws_persist = off;
+  for (size_t id = L; id < p->tensors.size(); ++id)
+    if (pinned[id]) {
+      off = align_up(off, 256);
+      p->tensors[id].offset = off;
+      off += size_t(8) << p->tensors[id].rank;
+    }
+  p->ws_persist_bytes = off - p->ws_persist;
   size_t arena_base = align_up(off, 256);
   // first-fit arena over step outputs with liveness (an output lives until the
   // step that consumes it; the root lives to the end)
@@ -163,7 +189,7 @@ void layout_steps(Plan* p) {
                live.end());
   };
   for (auto& s : p->steps) {
-    p->tensors[s.out].offset = arena_base + alloc(size_t(8) << p->tensors[s.out].rank, s.out);
+    if (!pinned[s.out]) p->tensors[s.out].offset = arena_base + alloc(size_t(8) << p->tensors[s.out].rank, s.out);
     if (s.a >= L) release(s.a);
     if (s.b >= L) release(s.b);
   }

@@ -62,7 +62,16 @@ def test_plan_step_accounting(mode, w):
     assert info["n_steps"] == info["n_leaves"] - 1
     flops = sum(8.0 * 2.0 ** (r[3] + r[4] + r[5] + r[6]) for r in st)
     assert math.isclose(flops, info["flops_per_pass"], rel_tol=1e-12)
-    assert info["flops_per_batch"] == info["flops_per_pass"] * 2 ** info["n_sliced"]
+    # slice-invariant steps run once per batch, the rest once per slice
+    inv = [bool(r[7] & 4) for r in st]
+    per = [8.0 * 2.0 ** (r[3] + r[4] + r[5] + r[6]) for r in st]
+    want = sum(f if i else f * 2 ** info["n_sliced"] for f, i in zip(per, inv))
+    assert math.isclose(info["flops_per_batch"], want, rel_tol=1e-12)
+    if info["n_sliced"] == 0:
+        assert all(inv)
+    else:
+        assert not inv[-1]  # the root holds every leaf, sliced ones included
+
     # GEMM shape consistency: a = K+M+H bits, b = K+N+H bits, out = N+M+H bits
     for r in st:
         assert r[0] == r[6] + r[4] + r[3]
