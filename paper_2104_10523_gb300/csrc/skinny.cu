@@ -297,15 +297,21 @@ __global__ void __launch_bounds__(256) cgemm_rows_regk_kernel(const float2* __re
 // As cgemm_rows_regk_kernel, but the large operand is read in its stored bit
 // layout (no separate permute): row g (its N or M index, then batch bits) starts
 // at the source offset sum_j bit_j(g) << rowpos[j], and element k of a row is
-// koff[k] further on.  Leaves with sliced labels add the slice offset.
-template <int KMAX, int ROWS>
+// koff[k] further on.  Leaves with sliced labels add the slice offset.  The row
+// offset is split into the thread's low 8 row bits (computed once) and the
+// CTA's row-block bits above them (one deposit per block, in shared memory);
+// EXACT instances have K == KMAX at compile time, and the small operand is read
+// in 16-byte pairs of k.
+template <int KMAX, int ROWS, bool EXACT>
 __global__ void __launch_bounds__(256) cgemm_rows_gather_kernel(const float2* __restrict__ S,
                                                                 const float2* __restrict__ G, const GatherDesc gd,
                                                                 float2* __restrict__ C, double2* __restrict__ acc,
                                                                 int ns, int ng, int K, int batch, long long s_stride,
                                                                 long long g_stride, int tiles_g, int slice_id) {
-  __shared__ float2 Ss[RW_SMAX][KMAX];
+  static_assert(KMAX % 2 == 0, "pairs of k");
+  __shared__ __align__(16) float2 Ss[RW_SMAX][KMAX];
   __shared__ uint32_t koff[KMAX];
+  __shared__ unsigned long long hib[ROWS];
   const int tile = int(blockIdx.x % tiles_g);
   const int h = int(blockIdx.x / tiles_g);
   const float2* Sh = S + size_t(h) * ns * K;
@@ -319,9 +325,23 @@ __global__ void __launch_bounds__(256) cgemm_rows_gather_kernel(const float2* __
       if ((kk >> j) & 1) o |= 1u << gd.kpos[j];
     koff[kk] = o;
   }
+  // rows of block r: (tile * ROWS + r) * 256 + threadIdx.x of batch entry h;
+  // with ng a multiple of 256 the global row index's low 8 bits are threadIdx.x
+  const bool split8 = gd.nrow >= 8 && (ng & 255) == 0;
+  if (split8 && threadIdx.x < ROWS) {
+    const long long hi = ((long long)h * ng + (long long)(tile * ROWS + int(threadIdx.x)) * 256) >> 8;
+    unsigned long long o = 0;
+    for (int j = 8; j < gd.nrow; ++j)
+      if ((hi >> (j - 8)) & 1) o |= 1ull << gd.rowpos[j];
+    hib[threadIdx.x] = o;
+  }
   size_t soff = 0;
   for (int j = 0; j < gd.n_slice; ++j)
     if (gd.slice_src[j] >= 0 && ((slice_id >> j) & 1)) soff |= size_t(1) << gd.slice_src[j];
+  size_t lo8 = 0;
+  if (split8)
+    for (int j = 0; j < 8; ++j)
+      if ((threadIdx.x >> j) & 1) lo8 |= size_t(1) << gd.rowpos[j];
   __syncthreads();
   const bool pairs = gd.nk >= 1 && gd.kpos[0] == 0;
   int g[ROWS];
@@ -331,53 +351,63 @@ __global__ void __launch_bounds__(256) cgemm_rows_gather_kernel(const float2* __
   for (int r = 0; r < ROWS; ++r) {
     g[r] = tile * 256 * ROWS + r * 256 + threadIdx.x;
     live[r] = g[r] < ng;
-    // global row index over (g, h): g's bits first, then the batch bits
-    const long long grow = (long long)h * ng + (live[r] ? g[r] : 0);
     size_t base = soff;
-    for (int j = 0; j < gd.nrow; ++j)
-      if ((grow >> j) & 1) base |= size_t(1) << gd.rowpos[j];
+    if (split8) {
+      base |= lo8 | size_t(hib[r]);
+    } else {
+      // global row index over (g, h): g's bits first, then the batch bits
+      const long long grow = (long long)h * ng + (live[r] ? g[r] : 0);
+      for (int j = 0; j < gd.nrow; ++j)
+        if ((grow >> j) & 1) base |= size_t(1) << gd.rowpos[j];
+    }
     if (pairs) {
       // the lowest K bit is the stored layout's stride-1 bit: pairs (k, k+1) are
       // adjacent and 16-byte aligned (every other offset bit is >= 1)
 #pragma unroll
-      for (int kk = 0; kk < KMAX; kk += 2)
-        if (kk < K) {
-          const float4 v = live[r] ? *reinterpret_cast<const float4*>(G + base + koff[kk])
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-          gv[r][kk] = make_float2(v.x, v.y);
-          gv[r][kk + 1] = make_float2(v.z, v.w);
-        }
+      for (int kk = 0; kk < KMAX; kk += 2) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((EXACT || kk < K) && live[r]) v = *reinterpret_cast<const float4*>(G + base + koff[kk]);
+        gv[r][kk] = make_float2(v.x, v.y);
+        gv[r][kk + 1] = make_float2(v.z, v.w);
+      }
     } else {
 #pragma unroll
       for (int kk = 0; kk < KMAX; ++kk)
-        if (kk < K) gv[r][kk] = live[r] ? G[base + koff[kk]] : make_float2(0.f, 0.f);
+        gv[r][kk] = ((EXACT || kk < K) && live[r]) ? G[base + koff[kk]] : make_float2(0.f, 0.f);
     }
   }
-  const size_t hbase = size_t(h) * ns * ng;
+  size_t obase[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) obase[r] = size_t(h) * ns * ng + size_t(g[r]) * g_stride;
 #pragma unroll
   for (int s = 0; s < RW_SMAX; ++s) {
     if (s >= ns) break;
     float ar[ROWS], ai[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) ar[r] = ai[r] = 0.f;
+    // values beyond K are zero on both sides, so whole pairs are summed
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) {
-      if (kk < K) {
-        const float2 a = Ss[s][kk];
+    for (int kk = 0; kk < KMAX; kk += 2) {
+      if (EXACT || kk < K) {
+        const float4 a2 = *reinterpret_cast<const float4*>(&Ss[s][kk]);
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
-          const float2 bb = gv[r][kk];
-          ar[r] = fmaf(a.x, bb.x, ar[r]);
-          ar[r] = fmaf(-a.y, bb.y, ar[r]);
-          ai[r] = fmaf(a.x, bb.y, ai[r]);
-          ai[r] = fmaf(a.y, bb.x, ai[r]);
+          const float2 b0 = gv[r][kk], b1 = gv[r][kk + 1];
+          ar[r] = fmaf(a2.x, b0.x, ar[r]);
+          ar[r] = fmaf(-a2.y, b0.y, ar[r]);
+          ai[r] = fmaf(a2.x, b0.y, ai[r]);
+          ai[r] = fmaf(a2.y, b0.x, ai[r]);
+          ar[r] = fmaf(a2.z, b1.x, ar[r]);
+          ar[r] = fmaf(-a2.w, b1.y, ar[r]);
+          ai[r] = fmaf(a2.z, b1.y, ai[r]);
+          ai[r] = fmaf(a2.w, b1.x, ai[r]);
         }
       }
     }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       if (!live[r]) continue;
-      const size_t o = hbase + size_t(s) * s_stride + size_t(g[r]) * g_stride;
+      const size_t o = obase[r] + size_t(s) * s_stride;
       if (acc) {
         double2 v = acc[o];
         v.x += ar[r];
@@ -404,15 +434,21 @@ cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const
   const float2* Gp = reinterpret_cast<const float2*>(Gsrc);
   float2* Cp = reinterpret_cast<float2*>(C);
   double2* Ap = reinterpret_cast<double2*>(acc);
-  if (K <= 8)
-    cgemm_rows_gather_kernel<8, 2><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
-                                                       g_stride_out, int(tg), slice_id);
-  else if (K <= 16)
-    cgemm_rows_gather_kernel<16, 1><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
-                                                        g_stride_out, int(tg), slice_id);
-  else
-    cgemm_rows_gather_kernel<32, 1><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,
-                                                        g_stride_out, int(tg), slice_id);
+#define TNQ_GATHER(KM, R, EX)                                                                               \
+  cgemm_rows_gather_kernel<KM, R, EX><<<g2, 256, 0, st>>>(Sp, Gp, gd, Cp, Ap, ns, ng, K, batch, s_stride_out,  \
+                                                          g_stride_out, int(tg), slice_id)
+  switch (K) {
+    case 2: TNQ_GATHER(2, 2, true); break;
+    case 4: TNQ_GATHER(4, 2, true); break;
+    case 8: TNQ_GATHER(8, 2, true); break;
+    case 16: TNQ_GATHER(16, 1, true); break;
+    case 32: TNQ_GATHER(32, 1, true); break;
+    default:
+      if (K <= 8) TNQ_GATHER(8, 2, false);
+      else if (K <= 16) TNQ_GATHER(16, 1, false);
+      else TNQ_GATHER(32, 1, false);
+  }
+#undef TNQ_GATHER
   return cudaGetLastError();
 }
 
