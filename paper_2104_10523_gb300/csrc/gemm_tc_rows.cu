@@ -28,9 +28,12 @@
 //   warps 0-7   converters, two groups of four; group g fills the stages of
 //               the CTA's tiles i = g, g + 2, ...: each thread owns one tile
 //               row and walks it in chunks of up to 16 complex values (loads
-//               of 16-byte pairs when the lowest stored bit is a K bit),
-//               splitting and storing one chunk while the loads of the next
-//               two (16-value chunks) or four (8-value chunks) are in flight;
+//               of 16-byte pairs when the lowest stored bit is a K bit); the
+//               loads of the next chunks are issued before the current one is
+//               split and stored, and the register ring rotates by moves,
+//               which wait for the newest load, so in effect one chunk is in
+//               flight across each split (an unrolled ring without the moves
+//               measured slower);
 //   warp 8      allocates TMEM and (one thread) issues the MMAs of each tile
 //               into one of the TMEM accumulator buffers;
 //   warps 9-12  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, 32
