@@ -19,4 +19,11 @@ Modules:
                   tensors over their shared labels (one step of Sec. 3.1).
   mlp          -- FP64 reference of the path cost model's MLP (forward,
                   backward, Adam).
+  golden       -- readers of the stored contraction trees and expected
+                  values (tests/golden).
+
+O2 also evaluates marginal wave-function slices (Sec. 4.4: qubits left open),
+the doubled density-matrix network of Sec. 3.3 (exact noisy probabilities),
+and follows a contraction tree given over groups of circuit tensors, with its
+own slicing, so that it can contract the 36-qubit benchmark circuit.
 """

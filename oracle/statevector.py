@@ -86,3 +86,17 @@ def probabilities_dm(circ, bitstrings) -> np.ndarray:
     rho = density_matrix(circ)
     bits = np.asarray(bitstrings, dtype=np.int64)
     return np.array([np.real(rho[tuple(b) + tuple(b)]) for b in bits])
+
+
+def wavefunction_slice(circ, bitstrings) -> np.ndarray:
+    """Marginal wave-function slices (Sec. 4.4): for each row x of bitstrings
+    [B][n] with -1 at the open qubits (the same ones in every row), the
+    amplitudes <x_fixed, y|U|0...0> for every value y of the open qubits, as
+    [B][2^k]; the open qubit with the lowest index is the most significant bit
+    of y."""
+    psi = final_state(circ)
+    rows = []
+    for b in np.asarray(bitstrings, dtype=np.int64):
+        idx = tuple(slice(None) if v == -1 else int(v) for v in b)
+        rows.append(np.ascontiguousarray(psi[idx]).reshape(-1))
+    return np.array(rows, dtype=np.complex128)

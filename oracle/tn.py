@@ -30,13 +30,23 @@ Tensor = Tuple[np.ndarray, List[int]]
 def build_network(circ, bitstring=None, kraus_picks=None) -> List[Tensor]:
     """Tensors of <x| U |0...0>; with bitstring=None the final qubit legs stay
     open (their labels are returned by open_labels())."""
+    return build_network_wires(circ, bitstring, kraus_picks)[0]
+
+
+def build_network_wires(circ, bitstring=None, kraus_picks=None):
+    """(tensors, wires): the network of build_network and the label of every
+    circuit wire, wires[(q, k)] = label of qubit q's wire after the k-th op
+    acting on q (k = 0: the |0> input)."""
     n = circ.n
     counter = itertools.count()
     wire = []
+    pos = [0] * n
+    wires = {}
     tensors: List[Tensor] = []
     for q in range(n):
         lab = next(counter)
         wire.append(lab)
+        wires[(q, 0)] = lab
         tensors.append((np.array([1.0, 0.0], dtype=np.complex128), [lab]))
     c = 0
     for op in circ.ops:
@@ -55,13 +65,17 @@ def build_network(circ, bitstring=None, kraus_picks=None) -> List[Tensor]:
         tensors.append((T, outs + [wire[q] for q in op.qubits]))
         for q, lab in zip(op.qubits, outs):
             wire[q] = lab
+            pos[q] += 1
+            wires[(q, pos[q])] = lab
     if bitstring is not None:
         for q in range(n):
+            if int(bitstring[q]) == -1:   # open qubit (Sec. 4.4): no projection
+                continue
             e = np.zeros(2, dtype=np.complex128)
             e[int(bitstring[q])] = 1.0
             tensors.append((e, [wire[q]]))
     build_network.last_open = list(wire)
-    return tensors
+    return tensors, wires
 
 
 def contract_pair(a: Tensor, b: Tensor) -> Tensor:
@@ -205,6 +219,18 @@ def amplitude(circ, bitstring, order: str = "greedy", seed: int = 0,
     return complex(np.asarray(val).reshape(()))
 
 
+def wavefunction_slice(circ, bitstring, order: str = "greedy", seed: int = 0) -> np.ndarray:
+    """Sec. 4.4: the network with the qubits marked -1 left open, contracted
+    to a tensor over their final wires; returned as a 2^k vector with the open
+    qubit of lowest index as the most significant bit."""
+    net = build_network(circ, bitstring)
+    open_labels = [build_network.last_open[q] for q in range(circ.n) if int(bitstring[q]) == -1]
+    o = greedy_order(net) if order == "greedy" else random_order(net, seed)
+    T, labs = contract(net, o)
+    T = np.asarray(T).reshape((2,) * len(labs)) if labs else np.asarray(T)
+    return np.ascontiguousarray(np.transpose(T, [labs.index(l) for l in open_labels])).reshape(-1)
+
+
 def amplitudes(circ, bitstrings, **kw) -> np.ndarray:
     return np.array([amplitude(circ, b, **kw) for b in np.asarray(bitstrings)],
                     dtype=np.complex128)
@@ -224,3 +250,151 @@ def order_cost(tensors: Sequence[Tensor], order) -> Tuple[float, int]:
         mx = max(mx, len(labs[nxt]))
         nxt += 1
     return flops, mx
+
+
+def order_from_groups(tensors: Sequence[Tensor], wires: dict, group_wires, pairs) -> List[Tuple[int, int]]:
+    """A pairwise order over this module's own network that follows a
+    contraction tree given over groups of circuit tensors (the grouping of
+    small gate tensors into larger ones of Sec. 3.1.1, then the pairwise
+    sequence of Sec. 3.1).
+
+    group_wires[i]: the circuit wires (qubit, position) that cross the boundary
+    of group i ((-1, -1) entries, batch indices, are ignored); pairs: the
+    tree's steps over group ids (groups 0..G-1, then the result of step j as
+    G + j).  The network is cut at every listed wire; each connected piece must
+    have exactly the listed boundary of one group.  Each piece is contracted
+    internally first (greedy_order), then the tree is followed.  The order does
+    not change the exact value of the contraction, only its cost.
+    """
+    cut = {wires[tuple(w)] for g in group_wires for w in g if w[0] >= 0}
+    parent = list(range(len(tensors)))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    holders = {}
+    for i, (_, labs) in enumerate(tensors):
+        for l in labs:
+            holders.setdefault(l, []).append(i)
+    for l, ids in holders.items():
+        if l not in cut:
+            for j in ids[1:]:
+                parent[find(j)] = find(ids[0])
+    pieces = {}
+    for i in range(len(tensors)):
+        pieces.setdefault(find(i), []).append(i)
+    by_boundary = {}
+    for members in pieces.values():
+        bnd = frozenset(l for i in members for l in tensors[i][1] if l in cut)
+        by_boundary.setdefault(bnd, []).append(members)
+    order: List[Tuple[int, int]] = []
+    nxt = len(tensors)
+    group_id = []
+    for g in group_wires:
+        key = frozenset(wires[tuple(w)] for w in g if w[0] >= 0)
+        if not by_boundary.get(key):
+            raise ValueError(f"no piece of the network has the boundary of group {len(group_id)}")
+        members = by_boundary[key].pop()
+        if len(members) == 1:
+            group_id.append(members[0])
+            continue
+        sub = [tensors[i] for i in members]
+        ids = list(members)
+        for a, b in greedy_order(sub):
+            order.append((ids[a], ids[b]))
+            ids.append(nxt)
+            nxt += 1
+        group_id.append(ids[-1])
+    if any(v for v in by_boundary.values()):
+        raise ValueError("network pieces left over that no group covers")
+    ids = list(group_id)
+    for a, b in pairs:
+        order.append((ids[int(a)], ids[int(b)]))
+        ids.append(nxt)
+        nxt += 1
+    return order
+
+
+def choose_slices(tensors: Sequence[Tensor], order, cap_log2: int) -> List[int]:
+    """Slicing (Sec. 3.1): pick indices to fix until no tensor met along
+    `order` has more than 2^cap_log2 elements.  Each round slices the label
+    held by the most tensors of the current largest rank (ties: lowest label)."""
+    sliced: List[int] = []
+    while True:
+        labs = {i: set(t[1]) - set(sliced) for i, t in enumerate(tensors)}
+        seen = list(labs.values())
+        nxt = len(tensors)
+        for i, j in order:
+            li, lj = labs.pop(i), labs.pop(j)
+            labs[nxt] = li ^ lj
+            seen.append(labs[nxt])
+            nxt += 1
+        top = max(len(x) for x in seen)
+        if top <= cap_log2:
+            return sliced
+        count = {}
+        for x in seen:
+            if len(x) == top:
+                for l in x:
+                    count[l] = count.get(l, 0) + 1
+        sliced.append(min(count, key=lambda l: (-count[l], l)))
+
+
+def build_density_network_wires(circ, bitstring):
+    """(tensors, wires): the doubled network of Sec. 3.3 whose value is
+    p(x) = <x|rho|x>.  Every qubit has a ket wire and a bra wire, both starting
+    in |0>; a gate U is the tensor U on the ket wires and its complex conjugate
+    on the bra wires; a one-qubit channel {A_k} (Eq. kraus_sum) is one rank-4
+    tensor joining the qubit's ket and bra wires, S[i, i', j, j'] =
+    sum_k A_k[i, j] conj(A_k[i', j']) (outputs i, i'; inputs j, j'); both wires
+    of qubit q end in <x_q|.  wires[(q, k)] / wires[(q + n, k)] name the ket /
+    bra wire of qubit q after the k-th op acting on it."""
+    n = circ.n
+    counter = itertools.count()
+    ket, bra, pos = [], [], [0] * n
+    wires = {}
+    tensors: List[Tensor] = []
+    for side, lst in ((0, ket), (n, bra)):
+        for q in range(n):
+            lab = next(counter)
+            lst.append(lab)
+            wires[(q + side, 0)] = lab
+            tensors.append((np.array([1.0, 0.0], dtype=np.complex128), [lab]))
+    for op in circ.ops:
+        k = len(op.qubits)
+        if op.kind == "gate":
+            U = np.asarray(op.mats[0], np.complex128)
+            for lst, M in ((ket, U), (bra, U.conj())):
+                outs = [next(counter) for _ in op.qubits]
+                tensors.append((M.reshape((2,) * (2 * k)), outs + [lst[q] for q in op.qubits]))
+                for q, lab in zip(op.qubits, outs):
+                    lst[q] = lab
+        else:
+            if k != 1:
+                raise ValueError("the doubled network takes one-qubit channels only")
+            q = op.qubits[0]
+            S = sum(np.einsum("ij,kl->ikjl", A, np.conj(A)) for A in op.mats)
+            o_ket, o_bra = next(counter), next(counter)
+            tensors.append((S, [o_ket, o_bra, ket[q], bra[q]]))
+            ket[q], bra[q] = o_ket, o_bra
+        for q in op.qubits:
+            pos[q] += 1
+            wires[(q, pos[q])] = ket[q]
+            wires[(q + n, pos[q])] = bra[q]
+    for lst in (ket, bra):
+        for q in range(n):
+            e = np.zeros(2, dtype=np.complex128)
+            e[int(bitstring[q])] = 1.0
+            tensors.append((e, [lst[q]]))
+    return tensors, wires
+
+
+def density_probability(circ, bitstring, order=None) -> float:
+    """<x|rho|x> by contracting the doubled network (real part; the imaginary
+    part is rounding)."""
+    net, _ = build_density_network_wires(circ, bitstring)
+    val = contract(net, order)[0]
+    return float(np.real(np.asarray(val).reshape(())))

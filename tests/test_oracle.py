@@ -165,6 +165,55 @@ def test_ghz_closed_form_tn(n):
         assert abs(sv.amplitudes(c, [[1] * n])[0] - g[("ghz", "all1")]) < 1e-14
 
 
+@pytest.mark.parametrize("n", [8, 60])
+def test_wavefunction_slice_cat_state_closed_form(n):
+    """Sec. 4.4, Fig. 9: the cat state (H then CX chain) with qubits 2 and
+    min(47, n-1) open.  Other qubits all 0 -> (1/sqrt2) [1,0,0,0], all 1 ->
+    (1/sqrt2) [0,0,0,1] (the paper prints the normalised vectors [1,0,0,0] and
+    [0,0,0,1]); any mixed assignment -> 0."""
+    c = ghz_circuit(n)
+    o2 = min(47, n - 1)
+    s = 1 / np.sqrt(2)
+    for fill, want in ((0, [s, 0, 0, 0]), (1, [0, 0, 0, s])):
+        bits = [fill] * n
+        bits[2] = bits[o2] = -1
+        got = tn.wavefunction_slice(c, bits)
+        assert np.allclose(got, want, atol=1e-15)
+        assert np.allclose(got / np.linalg.norm(got), np.array(want) / s, atol=1e-15)
+        if n <= 12:
+            assert np.allclose(sv.wavefunction_slice(c, [bits])[0], want, atol=1e-15)
+    bits = [0] * n
+    bits[2] = bits[o2] = -1
+    bits[n - 2 if n - 2 not in (2, o2) else 1] = 1
+    assert np.allclose(tn.wavefunction_slice(c, bits), 0, atol=1e-15)
+
+
+def test_wavefunction_slice_both_oracles_and_norm():
+    """O1's slice (statevector indexing) and O2's (network with open legs)
+    agree on a random grid circuit, and the slices over every assignment of
+    the fixed qubits hold the whole normalised state."""
+    c = grid_circuit(3, 3, 6, 31)
+    open_q = [1, 4, 8]
+    rows = []
+    for vals in itertools.product((0, 1), repeat=6):
+        b = [-1] * 9
+        for q, v in zip([q for q in range(9) if q not in open_q], vals):
+            b[q] = v
+        rows.append(b)
+    s1 = sv.wavefunction_slice(c, rows)
+    assert s1.shape == (64, 8)
+    assert abs(np.sum(np.abs(s1) ** 2) - 1.0) < 1e-13
+    for i in (0, 17, 63):
+        s2 = tn.wavefunction_slice(c, rows[i], order="random", seed=i)
+        assert np.allclose(s2, s1[i], atol=1e-14)
+    # entry y of the slice is the amplitude of the completed bitstring
+    full = np.array(rows[17])
+    y = 5
+    for k, q in enumerate(open_q):
+        full[q] = (y >> (len(open_q) - 1 - k)) & 1
+    assert abs(s1[17][y] - sv.amplitudes(c, [full])[0]) < 1e-15
+
+
 def test_norm_statevector_config_small():
     c = grid_circuit(3, 4, 8, 1234)
     psi = sv.final_state(c)
@@ -303,6 +352,37 @@ def test_depolarizing_hh_closed_form():
         c.gate(H, 0).channel(depolarizing(p), 0).gate(H, 0).channel(depolarizing(p), 0)
     pz = sv.probabilities_dm(c, [[0], [1]])
     assert abs((pz[0] - pz[1]) - (1 - 4 * p / 3) ** (2 * m)) < 1e-14
+
+
+def test_density_network_matches_density_matrix():
+    """O2's doubled network (Sec. 3.3) against O1's Kraus-sum density matrix
+    on a noisy grid circuit, plus the trace: the probabilities of all 2^n
+    bitstrings sum to 1."""
+    c = noisy_grid_circuit(2, 3, 4, seed=5, p_depol=0.05, gamma=0.08)
+    allbits = np.array(list(itertools.product((0, 1), repeat=6)))
+    exact = sv.probabilities_dm(c, allbits)
+    got = np.array([tn.density_probability(c, b) for b in allbits])
+    assert np.allclose(got, exact, atol=1e-14)
+    assert abs(got.sum() - 1.0) < 1e-13
+    net, _ = tn.build_density_network_wires(c, allbits[5])
+    v = tn.contract(net, tn.random_order(net, 3))[0]
+    assert abs(complex(np.asarray(v).reshape(())) - exact[5]) < 1e-14
+
+
+def test_density_network_closed_forms():
+    """Amplitude damping on |1> for m rounds: P(1) = (1 - gamma)^m; depolarizing
+    H-H (the shape of Fig. 8): <Z> = (1 - 4p/3)^(2m) -- through the doubled network."""
+    gamma, m = 0.07, 9
+    c = Circuit(1).gate(X, 0)
+    for _ in range(m):
+        c.channel(amplitude_damping(gamma), 0)
+    assert abs(tn.density_probability(c, [1]) - (1 - gamma) ** m) < 1e-14
+    p, m = 0.01, 7
+    c = Circuit(1)
+    for _ in range(m):
+        c.gate(H, 0).channel(depolarizing(p), 0).gate(H, 0).channel(depolarizing(p), 0)
+    z = tn.density_probability(c, [0]) - tn.density_probability(c, [1])
+    assert abs(z - (1 - 4 * p / 3) ** (2 * m)) < 1e-14
 
 
 def test_trajectory_estimator_exactly_unbiased():
