@@ -105,6 +105,7 @@ typedef struct {
   double bytes_per_pass;     /* algorithmic HBM bytes of the GEMM and permute steps */
   double search_ms;          /* host time of the path search and slicing */
   size_t workspace_bytes;    /* device bytes tnq_plan_bind needs */
+  int n_open;                /* open qubits (tnq_plan_create_open); 0 otherwise */
 } tnq_plan_info;
 
 /* ---- library ---------------------------------------------------------- */
@@ -136,6 +137,33 @@ int tnq_circuit_n_qubits(const tnq_circuit* c);
  * sliced indices (Sec. 3.1), and lay out every step.  No GPU work.
  * Errors: INVALID_ARG (bad options), PLAN_INFEASIBLE (cap cannot be met). */
 tnq_status tnq_plan_create(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_plan** out);
+/* As tnq_plan_create, but the n_open listed qubits keep their final wires
+ * open (Sec. 4.4, the marginal wave-function slice): their projections are
+ * left out, so the network evaluates, per bitstring of the other qubits, to
+ * the 2^n_open amplitudes <x_fixed, y| U |0...0> over all values y of the open
+ * qubits.  tnq_amplitudes on such a plan expects -1 exactly at the open
+ * qubits of every bitstring (the paper's marker of an open qubit) and returns
+ * 2^n_open amplitudes per bitstring.  The open indices count towards
+ * max_intermediate_log2 like the batch indices.  open_qubits: host, n_open
+ * distinct qubit indices, copied.  Errors: INVALID_ARG (n_open outside
+ * [0, 30], bad or repeated qubit), NOT_SUPPORTED (circuit with channels),
+ * PLAN_INFEASIBLE as tnq_plan_create, also when batch_log2 + n_open exceeds
+ * max_intermediate_log2. */
+tnq_status tnq_plan_create_open(const tnq_circuit* c, const tnq_plan_opts* opts, int n_open, const int* open_qubits,
+                                tnq_plan** out);
+/* Exact noisy probabilities through the doubled density-matrix network of
+ * Sec. 3.3 (Fig. 7a): the state |0><0| evolves as a tensor network on 2n
+ * wires (ket wire q, bra wire q + n); a gate U acts as U on its ket wires and
+ * conj(U) on its bra wires, and a one-qubit channel {A_k} (Eq. kraus_sum)
+ * becomes the superoperator S = sum_k A_k (x) conj(A_k), a rank-4 tensor
+ * joining the ket and bra wires of its qubit.  Closing both wires of every
+ * qubit with <x_q| gives p(x) = <x|rho|x> (the trace of Fig. 7b with a
+ * projector), evaluated with tnq_density_probabilities.  The plan finds a
+ * path and slices for the doubled network as tnq_plan_create does (opts as
+ * there; traj_log2 is ignored: nothing is sampled).  Errors: as
+ * tnq_plan_create; NOT_SUPPORTED for a channel on two qubits; INVALID_ARG when
+ * 2n exceeds 4096. */
+tnq_status tnq_plan_create_density(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_plan** out);
 void tnq_plan_destroy(tnq_plan* p);
 tnq_status tnq_plan_get_info(const tnq_plan* p, tnq_plan_info* info);
 /* Per-step shape record: for step i, writes 8 ints
@@ -144,6 +172,25 @@ tnq_status tnq_plan_get_info(const tnq_plan* p, tnq_plan_info* info);
  * marks a step whose subtree holds no sliced label (run once per batch).
  * rec must hold 8 * n_steps ints. */
 tnq_status tnq_plan_get_steps(const tnq_plan* p, int* rec);
+
+/* Contraction tree of a plan (Sec. 3.1: the sequence of pairwise
+ * contractions), exported so that an independent contractor can follow the
+ * same order.  pairs: [n_steps][2] ints, caller-owned; step i contracts the
+ * tensors with ids pairs[2i] and pairs[2i+1], where ids 0 .. n_leaves-1 are the
+ * plan's leaves and id n_leaves + j is the result of step j.  Sliced indices
+ * are not part of the tree (slicing fixes indices, Sec. 3.1; the tree is the
+ * same in every slice).  Errors: INVALID_ARG for NULL arguments. */
+tnq_status tnq_plan_get_tree(const tnq_plan* p, int* pairs);
+/* Indices of one leaf of a plan as circuit wires: wires[2j], wires[2j+1] =
+ * (qubit, position) of the leaf's j-th index, where position k is the qubit's
+ * wire right after the k-th op acting on it (0 = the |0> input; the last
+ * position is the wire the bitstring projection closes, Sec. 3.1.1), and
+ * (-1, -1) marks a batch or trajectory index.  A leaf is a group of circuit
+ * ops merged into one tensor (Sec. 3.1.1), so its indices are the wires that
+ * cross its boundary.  wires: caller-owned, 2 * max ints; copies min(max, *n)
+ * entries and stores the leaf's rank in *n.
+ * Errors: INVALID_ARG for a leaf outside [0, n_leaves) or NULL arguments. */
+tnq_status tnq_plan_get_leaf_wires(const tnq_plan* p, int leaf, int max, int* wires, int* n);
 
 /* ---- contexts and GPU execution ----------------------------------------- */
 /* Errors: NO_DEVICE when the device is missing or not compute capability 10.3. */
@@ -161,8 +208,12 @@ tnq_status tnq_plan_bind(tnq_ctx* ctx, tnq_plan* p, void* workspace, size_t byte
  * bits: [n_bs][n_qubits] int8, host or device.  out: [n_bs][2] double (re, im),
  * host or device.  Bitstrings are processed 2^batch_log2 at a time, every
  * slice of a batch summed in FP64 in ascending slice order.
- * Errors: INVALID_ARG (bit not 0/1, plan built for a noisy circuit),
- * WORKSPACE (plan not bound), CUDA. */
+ * For a plan with open qubits (tnq_plan_create_open, Sec. 4.4) bits must hold
+ * -1 exactly at the open qubits and out is [n_bs][2^n_open][2]: entry o of a
+ * bitstring is the amplitude with the open qubits set to the bits of o, the
+ * first open qubit (lowest index) the most significant bit of o.
+ * Errors: INVALID_ARG (bit not 0/1, or not -1 at an open qubit; plan built
+ * for a noisy circuit), WORKSPACE (plan not bound), CUDA. */
 tnq_status tnq_amplitudes(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t* bits,
                           double* out);
 
@@ -174,6 +225,15 @@ tnq_status tnq_amplitudes(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t*
  * range outside [0, 2^n_sliced), otherwise as tnq_amplitudes. */
 tnq_status tnq_amplitudes_slices(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t* bits,
                                  int64_t slice_begin, int64_t slice_count, double* out);
+
+/* Exact probabilities p(x) = <x|rho|x> of a density-matrix plan
+ * (tnq_plan_create_density) for n_bs bitstrings of the circuit's n qubits.
+ * bits: [n_bs][n] int8, host or device; p_out: [n_bs] double, host or device.
+ * Bitstrings are processed 2^batch_log2 at a time; slices are summed in FP64
+ * as for amplitudes.  p(x) is real; rounding leaves an imaginary part that is
+ * dropped.  Errors: INVALID_ARG (not a density-matrix plan, bit not 0/1),
+ * WORKSPACE, CUDA. */
+tnq_status tnq_density_probabilities(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t* bits, double* p_out);
 
 /* Noisy probabilities p(x) = <x|rho|x> estimated from n_traj stochastic
  * trajectories (Eq. kraus_sum channels, one Kraus operator drawn per channel
@@ -240,6 +300,17 @@ tnq_status tnq_plan_autotune(tnq_ctx* ctx, tnq_plan* p, int reps, int* n_tensor_
  * results are identical either way.  Ragged last batches and timed runs
  * (tnq_ctx_set_timing) always launch directly. */
 tnq_status tnq_ctx_set_graphs(tnq_ctx* ctx, int enable);
+
+/* Which kernels run the steps of a plan.  TNQ_KERNELS_DEFAULT: the plan's
+ * autotuned choice for the context's precision if it has one, else the
+ * built-in rule (small, skinny and dot-shaped steps stay on the CUDA cores in
+ * FP32, since they are launch- or bandwidth-bound).  TNQ_KERNELS_TENSOR_CORES:
+ * in a tensor-core precision, every step that a tensor-core kernel accepts runs
+ * there (the tall-skinny kernel where its shape rules hold, else the general
+ * tensor-core GEMM); the others keep the built-in rule.  Results stay within
+ * the precision's bound either way.  Errors: INVALID_ARG for another value. */
+enum { TNQ_KERNELS_DEFAULT = 0, TNQ_KERNELS_TENSOR_CORES = 1 };
+tnq_status tnq_ctx_set_kernel_policy(tnq_ctx* ctx, int policy);
 
 /* ---- learned path cost model ----------------------------------------------- */
 /* A 3-layer MLP (d_in -> hidden -> hidden -> 1, ReLU; BF16 weights with FP32

@@ -153,6 +153,89 @@ tnq_status tnq_plan_create(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_
   return TNQ_OK;
 }
 
+tnq_status tnq_plan_create_open(const tnq_circuit* c, const tnq_plan_opts* opts, int n_open, const int* open_qubits,
+                                tnq_plan** out) {
+  if (!c || !opts || !out || (n_open > 0 && !open_qubits)) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (n_open < 0 || n_open > 30) return fail(TNQ_ERR_INVALID_ARG, "n_open must be in [0, 30]");
+  if (c->c.n_channels > 0) return fail(TNQ_ERR_NOT_SUPPORTED, "open qubits on a circuit with channels");
+  NetworkSpec spec;
+  spec.open.assign(c->c.n, 0);
+  for (int i = 0; i < n_open; ++i) {
+    const int q = open_qubits[i];
+    if (q < 0 || q >= c->c.n) return fail(TNQ_ERR_INVALID_ARG, "open qubit out of range");
+    if (spec.open[q]) return fail(TNQ_ERR_INVALID_ARG, "open qubit listed twice");
+    spec.open[q] = 1;
+  }
+  if (opts->batch_log2 + n_open > opts->max_intermediate_log2)
+    return fail(TNQ_ERR_PLAN_INFEASIBLE, "batch bits plus open qubits exceed max_intermediate_log2");
+  auto* p = new (std::nothrow) tnq_plan();
+  if (!p) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  tnq_status s = make_plan(c->c, *opts, &p->p, spec);
+  if (s != TNQ_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return TNQ_OK;
+}
+
+// Doubled circuit of Sec. 3.3 on 2n wires: ket wire q, bra wire q + n.  A gate
+// U acts as U on the ket wires and conj(U) on the bra wires; a one-qubit
+// channel {A_k} on q becomes the superoperator S = sum_k A_k (x) conj(A_k) on
+// (q, q + n), S[(i i'), (j j')] = sum_k A_k[i][j] conj(A_k[i'][j']).  The state
+// starts in |0...0>|0...0> (rho = |0><0|) and <<x, x| of the result is p(x).
+static tnq_status doubled_circuit(const Circuit& c, Circuit* d) {
+  const int n = c.n;
+  d->n = 2 * n;
+  d->ops.clear();
+  d->n_channels = 0;
+  for (const COp& op : c.ops) {
+    if (!op.channel) {
+      COp ket = op;
+      COp bra = op;
+      for (auto& z : bra.mats[0]) z = std::conj(z);
+      for (auto& q : bra.qubits) q += n;
+      d->ops.push_back(std::move(ket));
+      d->ops.push_back(std::move(bra));
+      continue;
+    }
+    if (op.qubits.size() != 1) return fail(TNQ_ERR_NOT_SUPPORTED, "two-qubit channels in a density-matrix network");
+    std::vector<cd> S(16, cd(0, 0));
+    for (const auto& A : op.mats)
+      for (int i = 0; i < 2; ++i)
+        for (int ip = 0; ip < 2; ++ip)
+          for (int j = 0; j < 2; ++j)
+            for (int jp = 0; jp < 2; ++jp) S[(i * 2 + ip) * 4 + (j * 2 + jp)] += A[i * 2 + j] * std::conj(A[ip * 2 + jp]);
+    COp sup;
+    sup.qubits = {op.qubits[0], op.qubits[0] + n};
+    sup.mats = {S};
+    d->ops.push_back(std::move(sup));
+  }
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_create_density(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_plan** out) {
+  if (!c || !opts || !out) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (2 * c->c.n > 4096) return fail(TNQ_ERR_INVALID_ARG, "doubled network exceeds 4096 wires");
+  Circuit d;
+  tnq_status s = doubled_circuit(c->c, &d);
+  if (s != TNQ_OK) return s;
+  auto* p = new (std::nothrow) tnq_plan();
+  if (!p) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  NetworkSpec spec;
+  spec.row_len = c->c.n;
+  tnq_plan_opts o = *opts;
+  o.traj_log2 = 0;
+  s = make_plan(d, o, &p->p, spec);
+  if (s != TNQ_OK) {
+    delete p;
+    return s;
+  }
+  p->p.density = true;
+  *out = p;
+  return TNQ_OK;
+}
+
 void tnq_plan_destroy(tnq_plan* p) {
   if (!p) return;
   plan_release_graph(&p->p);
@@ -177,6 +260,7 @@ tnq_status tnq_plan_get_info(const tnq_plan* pp, tnq_plan_info* info) {
   info->bytes_per_pass = p.cost.bytes;
   info->search_ms = p.search_ms;
   info->workspace_bytes = p.ws_total;
+  info->n_open = (int)p.net.open_qubits.size();
   return TNQ_OK;
 }
 
@@ -195,6 +279,29 @@ tnq_status tnq_plan_get_steps(const tnq_plan* pp, int* rec) {
     r[5] = s.nN;
     r[6] = s.nK;
     r[7] = (s.a < L ? 1 : 0) | (s.b < L ? 2 : 0) | (s.invariant ? 4 : 0);
+  }
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_get_tree(const tnq_plan* pp, int* pairs) {
+  if (!pp || !pairs) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  const Tree& t = pp->p.tree;
+  for (size_t i = 0; i < t.nodes.size(); ++i) {
+    pairs[2 * i] = t.nodes[i].first;
+    pairs[2 * i + 1] = t.nodes[i].second;
+  }
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_get_leaf_wires(const tnq_plan* pp, int leaf, int max, int* wires, int* n) {
+  if (!pp || !n || (max > 0 && !wires)) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  const Network& net = pp->p.net;
+  if (leaf < 0 || leaf >= (int)net.leaves.size()) return fail(TNQ_ERR_INVALID_ARG, "leaf index out of range");
+  const auto& labs = net.leaves[leaf].labels;
+  *n = (int)labs.size();
+  for (int j = 0; j < max && j < (int)labs.size(); ++j) {
+    wires[2 * j] = net.label_qubit[labs[j]];
+    wires[2 * j + 1] = net.label_pos[labs[j]];
   }
   return TNQ_OK;
 }
@@ -243,12 +350,20 @@ tnq_status tnq_plan_bind(tnq_ctx* c, tnq_plan* p, void* ws, size_t bytes) {
 
 tnq_status tnq_amplitudes(tnq_ctx* c, tnq_plan* p, int64_t n_bs, const int8_t* bits, double* out) {
   if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (p->p.density) return fail(TNQ_ERR_INVALID_ARG, "density-matrix plan; use tnq_density_probabilities");
   return exec_amplitudes(&c->c, &p->p, n_bs, bits, out);
+}
+
+tnq_status tnq_density_probabilities(tnq_ctx* c, tnq_plan* p, int64_t n_bs, const int8_t* bits, double* p_out) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (!p->p.density) return fail(TNQ_ERR_INVALID_ARG, "plan is not a density-matrix plan (tnq_plan_create_density)");
+  return exec_amplitudes(&c->c, &p->p, n_bs, bits, p_out);
 }
 
 tnq_status tnq_amplitudes_slices(tnq_ctx* c, tnq_plan* p, int64_t n_bs, const int8_t* bits, int64_t slice_begin,
                                  int64_t slice_count, double* out) {
   if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (p->p.density) return fail(TNQ_ERR_INVALID_ARG, "density-matrix plan; use tnq_density_probabilities");
   return exec_amplitudes_range(&c->c, &p->p, n_bs, bits, slice_begin, slice_count, out);
 }
 
@@ -398,6 +513,14 @@ tnq_status tnq_plan_autotune(tnq_ctx* c, tnq_plan* p, int reps, int* n_tensor_co
 tnq_status tnq_ctx_set_graphs(tnq_ctx* c, int enable) {
   if (!c) return fail(TNQ_ERR_INVALID_ARG, "NULL context");
   c->c.use_graphs = enable != 0;
+  return TNQ_OK;
+}
+
+tnq_status tnq_ctx_set_kernel_policy(tnq_ctx* c, int policy) {
+  if (!c) return fail(TNQ_ERR_INVALID_ARG, "NULL context");
+  if (policy != TNQ_KERNELS_DEFAULT && policy != TNQ_KERNELS_TENSOR_CORES)
+    return fail(TNQ_ERR_INVALID_ARG, "unknown kernel policy");
+  c->c.kernel_policy = policy;
   return TNQ_OK;
 }
 

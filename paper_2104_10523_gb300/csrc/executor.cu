@@ -112,6 +112,65 @@ cudaError_t perm(Ctx* ctx, const PermDesc& d, const void* src, void* dst0, void*
   return e;
 }
 
+// Projection leaves of a bound plan: they sit one after another at equal
+// stride (same rank), leaf j reading bitstring-row entry proj_src[j].
+struct ProjLeaves {
+  char* base = nullptr;
+  size_t stride = 0;
+  int n_proj = 0, n_open = 0, row_len = 0;
+  const int* tab = nullptr;
+};
+
+ProjLeaves proj_leaves(const Plan* p, char* ws) {
+  ProjLeaves r;
+  const int L = p->tree.n_leaves;
+  int first = -1;
+  for (int i = 0; i < L; ++i)
+    if (p->net.leaves[i].kind == LEAF_PROJ) {
+      first = i;
+      break;
+    }
+  r.n_proj = (int)p->net.proj_src.size();
+  r.n_open = (int)p->net.open_qubits.size();
+  r.row_len = p->net.row_len;
+  r.tab = reinterpret_cast<const int*>(ws + p->ws_qtab);
+  if (first >= 0) {
+    r.base = ws + p->tensors[first].offset;
+    r.stride = first + 1 < L ? p->tensors[first + 1].offset - p->tensors[first].offset : 0;
+  }
+  return r;
+}
+
+cudaError_t fill_projections(Ctx* ctx, const ProjLeaves& pl, int w, const int8_t* bits, int64_t nv, int* err) {
+  ctx->launches++;
+  return launch_proj_fill(pl.base, pl.stride, pl.n_proj, pl.n_open, pl.tab, pl.row_len, w, bits, nv, err,
+                          ctx->stream);
+}
+
+// Root positions of the batch labels (bit j of the bitstring index) and of
+// the open qubits' labels (in increasing qubit order).
+void root_positions(const Plan* p, std::vector<int>* bpos, std::vector<int>* opos) {
+  const auto& rl = p->tensors[p->root].labels;
+  auto at = [&](int l) { return int(std::find(rl.begin(), rl.end(), l) - rl.begin()); };
+  bpos->clear();
+  opos->clear();
+  for (int l : p->net.batch_labels) bpos->push_back(at(l));
+  for (int l : p->net.open_labels) opos->push_back(at(l));
+}
+
+// Host-side check of host bitstrings: -1 exactly at the open qubits, 0/1 elsewhere.
+bool host_bits_ok(const Plan* p, int64_t n_bs, const int8_t* bits) {
+  const int rl = p->net.row_len;
+  std::vector<char> open(rl, 0);
+  for (int q : p->net.open_qubits) open[q] = 1;
+  for (int64_t b = 0; b < n_bs; ++b)
+    for (int q = 0; q < rl; ++q) {
+      const int8_t x = bits[b * rl + q];
+      if (open[q] ? x != -1 : (x != 0 && x != 1)) return false;
+    }
+  return true;
+}
+
 // Prepare operands (permute / convert) and run one batched complex GEMM.
 tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_labels, bool perm_a,
                          const void* b_src, const std::vector<int>& b_labels, bool perm_b,
@@ -354,14 +413,29 @@ tnq_status run_step(Ctx* ctx, Plan* p, size_t si, int slice_id, char* ws, int ch
                        ws + p->ws_partial, choice);
 }
 
+// Kernel choice of a step under TNQ_KERNELS_TENSOR_CORES: the tall-skinny
+// tensor-core kernel where the shape qualifies, else the general tensor-core
+// GEMM where it is supported, else the default rule.
+int forced_tc_choice(const Ctx* ctx, const Step& s) {
+  if (ctx->precision == TNQ_PREC_FP32) return -1;
+  const int n_small = std::min(s.nM, s.nN), n_big = std::max(s.nM, s.nN);
+  if (n_small <= 7 && !use_dot(s.nM, s.nN, s.nK) &&
+      tc_rows_supported(1 << n_small, 1 << n_big, 1 << s.nK, 1 << s.nH, n_big + s.nH, ctx->precision))
+    return 2;
+  if (tc_gemm_supported(1 << s.nM, 1 << s.nN, 1 << s.nK, ctx->precision)) return 1;
+  return -1;
+}
+
 // One slice of a batch; slice-invariant steps run only in the batch's first
 // slice (their outputs persist for the batch).
 tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws, bool first) {
   const bool tuned = p->tuned_precision == ctx->precision && p->kernel_choice.size() == p->steps.size();
+  const bool forced = ctx->kernel_policy == TNQ_KERNELS_TENSOR_CORES;
   for (size_t si = 0; si < p->steps.size(); ++si) {
     if (p->steps[si].invariant && !first) continue;
     ctx->cur_step = (int)si;
-    tnq_status st = run_step(ctx, p, si, slice_id, ws, tuned ? p->kernel_choice[si] : -1);
+    const int choice = forced ? forced_tc_choice(ctx, p->steps[si]) : tuned ? p->kernel_choice[si] : -1;
+    tnq_status st = run_step(ctx, p, si, slice_id, ws, choice);
     if (st != TNQ_OK) return st;
   }
   ctx->cur_step = -1;
@@ -375,41 +449,35 @@ void plan_release_graph(Plan* p) {
   if (p->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(p->graph_exec));
   p->graph_exec = nullptr;
   p->graph_precision = -1;
+  p->graph_policy = -1;
 }
 
 namespace {
 
 // Enqueue one full batch that reads its bitstrings from the staging buffer and
 // leaves its amplitudes (bitstring order) in the output staging buffer.
-tnq_status enqueue_batch(Ctx* ctx, Plan* p, int64_t nv, const int* pos) {
+tnq_status enqueue_batch(Ctx* ctx, Plan* p, int64_t nv) {
   char* ws = static_cast<char*>(p->bound_ws);
-  const int n = p->net.n_qubits, w = p->batch_log2;
-  const int L = p->tree.n_leaves;
-  int first_proj = -1;
-  for (int i = 0; i < L; ++i)
-    if (p->net.leaves[i].kind == LEAF_PROJ) {
-      first_proj = i;
-      break;
-    }
-  size_t stride = first_proj + 1 < L ? p->tensors[first_proj + 1].offset - p->tensors[first_proj].offset : 0;
-  TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w,
-                            reinterpret_cast<const int8_t*>(ws + p->ws_bits), nv, reinterpret_cast<int*>(ws + p->ws_misc),
-                            ctx->stream));
-  ctx->launches++;
+  const int w = p->batch_log2;
+  std::vector<int> bpos, opos;
+  root_positions(p, &bpos, &opos);
+  TNQ_CUDA(fill_projections(ctx, proj_leaves(p, ws), w, reinterpret_cast<const int8_t*>(ws + p->ws_bits), nv,
+                            reinterpret_cast<int*>(ws + p->ws_misc)));
   TNQ_CUDA(launch_zero(ws + p->ws_acc, 16 * (size_t(1) << p->tensors[p->root].rank), ctx->stream));
   const int n_slices = 1 << p->slice_labels.size();
   for (int s = 0; s < n_slices; ++s) {
     tnq_status st = run_pass(ctx, p, s, ws, s == 0);
     if (st != TNQ_OK) return st;
   }
-  TNQ_CUDA(launch_finalize(ws + p->ws_acc, ws + p->ws_out_stage, nv, pos, w, ctx->stream));
+  TNQ_CUDA(launch_finalize(ws + p->ws_acc, ws + p->ws_out_stage, nv, bpos.data(), w, opos.data(), (int)opos.size(),
+                           p->density, ctx->stream));
   ctx->launches++;
   return TNQ_OK;
 }
 
 // Capture enqueue_batch for a full batch into a graph (once per plan and precision).
-tnq_status ensure_graph(Ctx* ctx, Plan* p, const int* pos) {
-  if (p->graph_exec && p->graph_precision == ctx->precision) return TNQ_OK;
+tnq_status ensure_graph(Ctx* ctx, Plan* p) {
+  if (p->graph_exec && p->graph_precision == ctx->precision && p->graph_policy == ctx->kernel_policy) return TNQ_OK;
   plan_release_graph(p);
   auto t0 = std::chrono::steady_clock::now();
   if (ctx->precision != TNQ_PREC_FP32) TNQ_CUDA(tc_gemm_prepare());
@@ -424,7 +492,7 @@ tnq_status ensure_graph(Ctx* ctx, Plan* p, const int* pos) {
     ctx->stream = user_stream;
     return cuda_fail(e, "cudaStreamBeginCapture");
   }
-  tnq_status st = enqueue_batch(ctx, p, int64_t(1) << p->batch_log2, pos);
+  tnq_status st = enqueue_batch(ctx, p, int64_t(1) << p->batch_log2);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(ctx->stream, &g);
   ctx->stream = user_stream;
@@ -442,6 +510,7 @@ tnq_status ensure_graph(Ctx* ctx, Plan* p, const int* pos) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   p->graph_exec = ex;
   p->graph_precision = ctx->precision;
+  p->graph_policy = ctx->kernel_policy;
   p->graph_nodes = (int64_t)nodes;
   p->graph_capture_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return TNQ_OK;
@@ -487,6 +556,14 @@ tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes) {
                                cudaMemcpyHostToDevice, ctx->stream));
     TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
   }
+  {
+    std::vector<int> tab = p->net.proj_src;
+    tab.insert(tab.end(), p->net.open_qubits.begin(), p->net.open_qubits.end());
+    if (!tab.empty()) {
+      TNQ_CUDA(cudaMemcpyAsync(base + p->ws_qtab, tab.data(), 4 * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+      TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+  }
   p->bound_ws = ws;
   p->bound_bytes = bytes;
   return TNQ_OK;
@@ -504,27 +581,21 @@ tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* 
   if (n_bs == 0) return TNQ_OK;
   TNQ_CUDA(cudaSetDevice(ctx->device));
   char* ws = static_cast<char*>(p->bound_ws);
-  const int n = p->net.n_qubits, w = p->batch_log2;
+  const int rl = p->net.row_len, w = p->batch_log2;
   const int64_t per = int64_t(1) << w;
+  const int64_t n_out = int64_t(1) << p->net.open_qubits.size();  // amplitudes per bitstring
+  const int64_t vals = p->density ? 1 : 2;                          // doubles per result
   const bool bits_dev = is_device_ptr(bits), out_dev = is_device_ptr(out);
-  if (!bits_dev)
-    for (int64_t i = 0; i < n_bs * n; ++i)
-      if (bits[i] != 0 && bits[i] != 1) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  if (!bits_dev && !host_bits_ok(p, n_bs, bits))
+    return fail(TNQ_ERR_INVALID_ARG, p->net.open_qubits.empty()
+                                         ? "bitstring entries must be 0 or 1"
+                                         : "bitstring entries must be -1 at the plan's open qubits and 0 or 1 elsewhere");
   int* err_flag = reinterpret_cast<int*>(ws + p->ws_misc);
   int8_t* bits_stage = reinterpret_cast<int8_t*>(ws + p->ws_bits);
   double* out_stage = reinterpret_cast<double*>(ws + p->ws_out_stage);
-  const int L = p->tree.n_leaves;
-  int first_proj = -1;
-  for (int i = 0; i < L; ++i)
-    if (p->net.leaves[i].kind == LEAF_PROJ) {
-      first_proj = i;
-      break;
-    }
-  size_t stride = first_proj + 1 < L ? p->tensors[first_proj + 1].offset - p->tensors[first_proj].offset : 0;
-  std::vector<int> pos(w);
-  const auto& rl = p->tensors[p->root].labels;
-  for (int j = 0; j < w; ++j)
-    pos[j] = int(std::find(rl.begin(), rl.end(), p->net.batch_labels[j]) - rl.begin());
+  const ProjLeaves pl = proj_leaves(p, ws);
+  std::vector<int> bpos, opos;
+  root_positions(p, &bpos, &opos);
   TNQ_CUDA(cudaMemsetAsync(err_flag, 0, 2 * sizeof(int), ctx->stream));
   const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
   const int64_t n_slices = int64_t(1) << p->slice_labels.size();
@@ -534,37 +605,38 @@ tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* 
   const bool graphs = ctx->use_graphs && !ctx->timing && slice_begin == 0 && slice_count == n_slices;
   for (int64_t base = 0; base < n_bs; base += per) {
     int64_t nv = std::min<int64_t>(per, n_bs - base);
+    const size_t out_bytes = size_t(nv * n_out * vals) * 8;
     if (graphs && nv == per) {
       // full batch: stage the bitstrings, replay the captured graph, copy out
-      TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * n, size_t(nv) * n,
+      TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * rl, size_t(nv) * rl,
                                bits_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
-      tnq_status st = ensure_graph(ctx, p, pos.data());
+      tnq_status st = ensure_graph(ctx, p);
       if (st != TNQ_OK) return st;
       TNQ_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(p->graph_exec), ctx->stream));
       ctx->launches += uint64_t(p->graph_nodes);
-      TNQ_CUDA(cudaMemcpyAsync(out + 2 * base, out_stage, size_t(nv) * 16,
+      TNQ_CUDA(cudaMemcpyAsync(out + vals * base * n_out, out_stage, out_bytes,
                                out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
       continue;
     }
     const int8_t* bsrc;
     if (bits_dev) {
-      bsrc = bits + base * n;
+      bsrc = bits + base * rl;
     } else {
-      TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * n, size_t(nv) * n, cudaMemcpyHostToDevice, ctx->stream));
+      TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * rl, size_t(nv) * rl, cudaMemcpyHostToDevice, ctx->stream));
       bsrc = bits_stage;
     }
-    TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w, bsrc, nv, err_flag, ctx->stream));
-    ctx->launches++;
+    TNQ_CUDA(fill_projections(ctx, pl, w, bsrc, nv, err_flag));
     TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
     for (int64_t s = slice_begin; s < slice_begin + slice_count; ++s) {
       tnq_status st = run_pass(ctx, p, int(s), ws, s == slice_begin);
       if (st != TNQ_OK) return st;
     }
-    double* dst = out_dev ? out + 2 * base : out_stage;
-    TNQ_CUDA(launch_finalize(ws + p->ws_acc, dst, nv, pos.data(), w, ctx->stream));
+    double* dst = out_dev ? out + vals * base * n_out : out_stage;
+    TNQ_CUDA(launch_finalize(ws + p->ws_acc, dst, nv, bpos.data(), w, opos.data(), (int)opos.size(), p->density,
+                             ctx->stream));
     ctx->launches++;
     if (!out_dev)
-      TNQ_CUDA(cudaMemcpyAsync(out + 2 * base, out_stage, size_t(nv) * 16, cudaMemcpyDeviceToHost, ctx->stream));
+      TNQ_CUDA(cudaMemcpyAsync(out + vals * base * n_out, out_stage, out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
   }
   int herr[2] = {0, 0};
   TNQ_CUDA(cudaMemcpyAsync(herr, err_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -574,7 +646,10 @@ tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* 
     if (ts != TNQ_OK) return ts;
   }
   if (herr[1]) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired; results are invalid");
-  if (herr[0]) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  if (herr[0])
+    return fail(TNQ_ERR_INVALID_ARG, p->net.open_qubits.empty()
+                                         ? "bitstring entries must be 0 or 1"
+                                         : "bitstring entries must be -1 at the plan's open qubits and 0 or 1 elsewhere");
   return TNQ_OK;
 }
 
@@ -659,22 +734,14 @@ template <typename Consume, typename BatchEnd>
 tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, uint64_t seed, int64_t n_bs,
                         const int8_t* bits, Consume consume, BatchEnd batch_end) {
   char* ws = static_cast<char*>(p->bound_ws);
-  const int n = p->net.n_qubits, w = p->batch_log2, t = p->traj_log2;
+  const int n = p->net.row_len, w = p->batch_log2, t = p->traj_log2;
   const int64_t per = int64_t(1) << w, tper = int64_t(1) << t;
   const bool bits_dev = is_device_ptr(bits);
-  if (!bits_dev)
-    for (int64_t i = 0; i < n_bs * n; ++i)
-      if (bits[i] != 0 && bits[i] != 1) return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
+  if (!bits_dev && !host_bits_ok(p, n_bs, bits))
+    return fail(TNQ_ERR_INVALID_ARG, "bitstring entries must be 0 or 1");
   int* err_flag = reinterpret_cast<int*>(ws + p->ws_misc);
   int8_t* bits_stage = reinterpret_cast<int8_t*>(ws + p->ws_bits);
-  const int L = p->tree.n_leaves;
-  int first_proj = -1;
-  for (int i = 0; i < L; ++i)
-    if (p->net.leaves[i].kind == LEAF_PROJ) {
-      first_proj = i;
-      break;
-    }
-  size_t stride = first_proj + 1 < L ? p->tensors[first_proj + 1].offset - p->tensors[first_proj].offset : 0;
+  const ProjLeaves pl = proj_leaves(p, ws);
   const auto& rl = p->tensors[p->root].labels;
   std::vector<int> bpos(w), tpos(t);
   for (int j = 0; j < w; ++j) bpos[j] = int(std::find(rl.begin(), rl.end(), p->net.batch_labels[j]) - rl.begin());
@@ -691,8 +758,7 @@ tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, u
       TNQ_CUDA(cudaMemcpyAsync(bits_stage, bits + base * n, size_t(nv) * n, cudaMemcpyHostToDevice, ctx->stream));
       bsrc = bits_stage;
     }
-    TNQ_CUDA(launch_proj_fill(ws + p->tensors[first_proj].offset, stride, n, w, bsrc, nv, err_flag, ctx->stream));
-    ctx->launches++;
+    TNQ_CUDA(fill_projections(ctx, pl, w, bsrc, nv, err_flag));
     tnq_status st = consume(-1, base, nv, 0, 0, bpos, tpos);  // batch start
     if (st != TNQ_OK) return st;
     for (int64_t tb = 0; tb < n_traj; tb += tper) {
@@ -729,6 +795,7 @@ tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, u
 tnq_status noisy_checks(Plan* p, int64_t n_traj, int64_t n_bs, const int8_t* bits, const void* out) {
   if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
   if (!p->net.noisy) return fail(TNQ_ERR_INVALID_ARG, "plan is for a circuit without channels");
+  if (!p->net.open_qubits.empty()) return fail(TNQ_ERR_NOT_SUPPORTED, "noisy plans with open qubits");
   if (n_traj < 1) return fail(TNQ_ERR_INVALID_ARG, "n_traj must be >= 1");
   if (n_bs < 0 || (n_bs > 0 && (!bits || !out))) return fail(TNQ_ERR_INVALID_ARG, "bad bitstring/output buffers");
   return TNQ_OK;

@@ -31,6 +31,7 @@ struct Ctx {
   std::vector<std::pair<int, KernelRecord>> pending;  // (event index, record)
   std::vector<KernelRecord> records;
   int cur_step = -1;
+  int kernel_policy = 0;         // TNQ_KERNELS_DEFAULT or TNQ_KERNELS_TENSOR_CORES
   bool use_graphs = true;        // replay full batches from a captured CUDA graph
   cudaStream_t capture_stream = nullptr;  // private stream graphs are captured on
 };

@@ -71,10 +71,23 @@ struct Network {
   std::vector<char> is_output;    // per label: kept to the end (batch labels)
   std::vector<int> batch_labels;  // bit j of the bitstring index within a pass
   std::vector<int> traj_labels;   // bit j of the trajectory index within a pass
+  // circuit wire of each label: qubit and position (position k = the qubit's
+  // wire after its k-th op, 0 = the |0> input); -1 for batch/trajectory labels
+  std::vector<int> label_qubit, label_pos;
+  // open qubits (no projection; their final wires are output labels), in
+  // increasing qubit order, and those output labels
+  std::vector<int> open_qubits, open_labels;
+  // projection leaf j reads entry proj_src[j] of a bitstring row of row_len
+  // entries (row_len = n_qubits, or the register size of a doubled network)
+  std::vector<int> proj_src;
+  int row_len = 0;
   bool noisy = false;
 };
 
-tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, Network* out);
+// open: per qubit, 1 = leave its final wire open.  row_len: entries per
+// bitstring row; projection leaf of qubit q reads entry q % row_len.
+tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, const std::vector<char>& open, int row_len,
+                         Network* out);
 
 // ---------------------------------------------------------------- path search
 struct Tree {
@@ -135,14 +148,18 @@ struct Plan {
   double search_ms = 0;
   int batch_log2 = 0, traj_log2 = 0;
   int root = -1;
+  // doubled density-matrix network (Sec. 3.3): results are the real numbers
+  // <<x, x|rho>> = p(x), written as one double per bitstring
+  bool density = false;
   // workspace layout (bytes)
   // persist: outputs of slice-invariant steps read by slice-dependent steps
   // (kept for the whole batch, outside the reusable arena)
   size_t ws_persist = 0, ws_persist_bytes = 0;
   size_t ws_leaves = 0, ws_arena = 0, ws_arena_bytes = 0, ws_scratch_a = 0, ws_scratch_b = 0, ws_partial = 0,
          ws_scratch_bytes = 0, ws_acc = 0, ws_misc = 0, ws_total = 0;
-  // misc region: [flags 256 B][bit staging][output staging 16 B x 2^w][psum][p2sum]
-  size_t ws_bits = 0, ws_out_stage = 0, ws_psum = 0, ws_p2sum = 0;
+  // misc region: [flags 256 B][bit staging][output staging 16 B x 2^(w + n_open)][psum][p2sum]
+  // [projection table: proj_src, then the row entries of the open qubits]
+  size_t ws_bits = 0, ws_out_stage = 0, ws_psum = 0, ws_p2sum = 0, ws_qtab = 0;
   // trajectory program (noisy circuits): tables uploaded at bind time
   std::vector<TrajLeafDesc> traj_leaves;
   std::vector<int> traj_leaf_ids;
@@ -162,6 +179,7 @@ struct Plan {
   // CUDA graph of one full batch (every slice and step), per precision
   void* graph_exec = nullptr;     // cudaGraphExec_t
   int graph_precision = -1;
+  int graph_policy = -1;          // kernel policy the graph was captured with
   double graph_capture_ms = 0;
   int64_t graph_nodes = 0;
   // device binding
@@ -170,10 +188,19 @@ struct Plan {
   int bound_precision = -1;
 };
 
-tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p);
+// Shape of the network a plan contracts beyond the plain amplitude network:
+// qubits left open (marginal wave-function slices) and the bitstring row
+// length (a doubled network reads each row twice).
+struct NetworkSpec {
+  std::vector<char> open;
+  int row_len = 0;
+};
+
+tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p, const NetworkSpec& spec = NetworkSpec());
 // A ranker returns the predicted time of one pass of a laid-out candidate plan.
 using CandidateRanker = std::function<tnq_status(const Plan&, double*)>;
-tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, const CandidateRanker* ranker);
+tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, const CandidateRanker* ranker,
+                            const NetworkSpec& spec = NetworkSpec());
 void layout_steps(Plan* p);
 
 }  // namespace tnq

@@ -516,17 +516,26 @@ cudaError_t launch_reduce_splits(const void* part, int splits, size_t n, void* C
 }
 
 // ------------------------------------------------------------------ projection fill
-__global__ void proj_fill_kernel(char* base, size_t stride, int n, int w, const int8_t* __restrict__ bits,
-                                 int64_t n_valid, int* err) {
+// Projection leaf j (at base + j * stride) gets P[x, b] = [bits[b][src[j]] == x]
+// (Sec. 3.1.1: <x_q| closes the qubit's final wire; b enumerates the bitstrings
+// of the pass).  Entries tab[n_proj .. n_proj + n_open) name the row entries of
+// open qubits, which must hold -1.  Any other value sets *err.
+__global__ void proj_fill_kernel(char* base, size_t stride, int n_proj, int n_open, const int* __restrict__ tab,
+                                 int row_len, int w, const int8_t* __restrict__ bits, int64_t n_valid, int* err) {
   const int64_t per = int64_t(1) << w;
-  const int64_t total = per * n;
+  const int64_t total = per * (n_proj + n_open);
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
-    int q = int(t / per);
-    int64_t b = t % per;
-    float2* P = reinterpret_cast<float2*>(base + stride * q);
+    const int j = int(t / per);
+    const int64_t b = t % per;
+    const int src = tab[j];
+    if (j >= n_proj) {
+      if (b < n_valid && bits[b * row_len + src] != -1) atomicOr(err, 1);
+      continue;
+    }
+    float2* P = reinterpret_cast<float2*>(base + stride * j);
     float v0 = 0.f, v1 = 0.f;
     if (b < n_valid) {
-      int8_t x = bits[b * n + q];
+      int8_t x = bits[b * row_len + src];
       if (x == 0) v0 = 1.f;
       else if (x == 1) v1 = 1.f;
       else atomicOr(err, 1);
@@ -536,40 +545,55 @@ __global__ void proj_fill_kernel(char* base, size_t stride, int n, int w, const 
   }
 }
 
-cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_qubits, int batch_log2,
-                             const int8_t* bits, int64_t n_valid, int* err_flag, cudaStream_t st) {
-  int64_t total = (int64_t(1) << batch_log2) * n_qubits;
+cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_proj, int n_open, const int* tab,
+                             int row_len, int batch_log2, const int8_t* bits, int64_t n_valid, int* err_flag,
+                             cudaStream_t st) {
+  int64_t total = (int64_t(1) << batch_log2) * (n_proj + n_open);
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  proj_fill_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<char*>(leaves_base), stride_bytes, n_qubits,
-                                           batch_log2, bits, n_valid, err_flag);
+  if (blocks < 1) return cudaSuccess;
+  proj_fill_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<char*>(leaves_base), stride_bytes, n_proj, n_open, tab,
+                                           row_len, batch_log2, bits, n_valid, err_flag);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ finalize
 struct PosTable {
-  int n;
+  int n, n_open;
   int pos[32];
+  int open_pos[32];
 };
 
-__global__ void finalize_kernel(const double2* __restrict__ acc, double2* __restrict__ out, int64_t n_valid,
-                                PosTable pt) {
-  for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < n_valid; b += int64_t(gridDim.x) * blockDim.x) {
+// out[b * 2^n_open + o] = acc[root index of (b, o)]: bit j of b sits at root
+// position pos[j]; open qubit i (i = 0 most significant in o) at open_pos[i].
+__global__ void finalize_kernel(const double2* __restrict__ acc, void* __restrict__ out, int64_t n_valid, PosTable pt,
+                                int real_only) {
+  const int64_t total = n_valid << pt.n_open;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = e >> pt.n_open;
+    const int64_t o = e & ((int64_t(1) << pt.n_open) - 1);
     size_t r = 0;
     for (int j = 0; j < pt.n; ++j)
       if ((b >> j) & 1) r |= size_t(1) << pt.pos[j];
-    out[b] = acc[r];
+    for (int i = 0; i < pt.n_open; ++i)
+      if ((o >> (pt.n_open - 1 - i)) & 1) r |= size_t(1) << pt.open_pos[i];
+    if (real_only)
+      reinterpret_cast<double*>(out)[e] = acc[r].x;
+    else
+      reinterpret_cast<double2*>(out)[e] = acc[r];
   }
 }
 
 cudaError_t launch_finalize(const void* acc, void* out, int64_t n_valid, const int* pos_table, int n_pos,
-                            cudaStream_t st) {
+                            const int* open_pos, int n_open, bool real_only, cudaStream_t st) {
   PosTable pt;
   pt.n = n_pos;
+  pt.n_open = n_open;
   for (int j = 0; j < n_pos && j < 32; ++j) pt.pos[j] = pos_table[j];
-  int blocks = (int)std::min<int64_t>((n_valid + 255) / 256, 1024);
+  for (int j = 0; j < n_open && j < 32; ++j) pt.open_pos[j] = open_pos[j];
+  const int64_t total = n_valid << n_open;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
-  finalize_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(acc), reinterpret_cast<double2*>(out),
-                                          n_valid, pt);
+  finalize_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(acc), out, n_valid, pt, real_only ? 1 : 0);
   return cudaGetLastError();
 }
 

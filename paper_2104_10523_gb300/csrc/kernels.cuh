@@ -87,14 +87,19 @@ cudaError_t launch_cgemm_rows_gather(const void* Ssmall, const void* Gsrc, const
                                      int ns, int ng, int K, int batch, long long s_stride_out, long long g_stride_out,
                                      int slice_id, cudaStream_t st);
 
-// Projection leaves: P_q[(b << 1) | x] = [bits[(base+b)*n + q] == x] for b < n_valid, else 0.
-cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_qubits, int batch_log2,
-                             const int8_t* bits, int64_t n_valid, int* err_flag, cudaStream_t st);
+// Projection leaves j < n_proj at leaves_base + j * stride_bytes:
+// P_j[(b << 1) | x] = [bits[b * row_len + tab[j]] == x] for b < n_valid, else 0.
+// tab (device) also lists, after the n_proj entries, the n_open row entries
+// that must hold -1 (open qubits).  Entries of another value set *err_flag.
+cudaError_t launch_proj_fill(void* leaves_base, size_t stride_bytes, int n_proj, int n_open, const int* tab,
+                             int row_len, int batch_log2, const int8_t* bits, int64_t n_valid, int* err_flag,
+                             cudaStream_t st);
 
-// out[b] = acc[root_index(b)] for b < n_valid (complex128), where
-// root_index(b) = sum_j bit_j(b) << pos[j].
-cudaError_t launch_finalize(const void* acc, void* out, int64_t n_valid, const int* pos_table,
-                            int n_pos, cudaStream_t st);
+// out[b * 2^n_open + o] = acc[root_index(b, o)] for b < n_valid (complex128;
+// only the real part, as one double, when real_only), where root_index =
+// sum_j bit_j(b) << pos[j] + sum_i bit_(n_open-1-i)(o) << open_pos[i].
+cudaError_t launch_finalize(const void* acc, void* out, int64_t n_valid, const int* pos_table, int n_pos,
+                            const int* open_pos, int n_open, bool real_only, cudaStream_t st);
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 

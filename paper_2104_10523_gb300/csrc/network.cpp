@@ -96,10 +96,12 @@ void contract_host(const Leaf& a, const Leaf& b, Leaf* out) {
 
 }  // namespace
 
-tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, Network* out) {
+tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, const std::vector<char>& open, int row_len,
+                         Network* out) {
   Network& net = *out;
   net = Network();
   net.n_qubits = c.n;
+  net.row_len = row_len > 0 ? row_len : c.n;
   const int n = c.n;
   const int nops = (int)c.ops.size();
   net.noisy = c.n_channels > 0;
@@ -153,20 +155,28 @@ tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, Networ
     gl[g].n_slots = (int)gqubits[g].size();
     gl[g].in_fixed_mask = 0;
   }
+  auto new_label = [&](int q, int pos) {
+    net.label_qubit.push_back(q);
+    net.label_pos.push_back(pos);
+    return next_label++;
+  };
   for (int q = 0; q < n; ++q) {
     auto& gs = groups_on[q];
+    int pos = 0;  // ops on q up to the current group boundary
     for (size_t j = 0; j < gs.size(); ++j) {
       int g = gs[j];
+      for (int i : members[g])
+        for (int qq : c.ops[i].qubits) pos += qq == q;
       int slot = gqubits[g][0] == q ? 0 : 1;
       if (j == 0) gl[g].in_fixed_mask |= 1 << slot;
       if (j + 1 < gs.size()) {
-        int l = next_label++;
+        int l = new_label(q, pos);
         gl[g].out_label[slot] = l;
         int g2 = gs[j + 1];
         int slot2 = gqubits[g2][0] == q ? 0 : 1;
         gl[g2].in_label[slot2] = l;
       } else {
-        int l = next_label++;
+        int l = new_label(q, pos);
         gl[g].out_label[slot] = l;
         final_label[q] = l;
       }
@@ -229,7 +239,7 @@ tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, Networ
     if (final_label[q] < 0) {
       Leaf L;
       L.kind = LEAF_STATIC;
-      int l = next_label++;
+      int l = new_label(q, 0);
       final_label[q] = l;
       L.labels = {l};
       L.data = {cd(1, 0), cd(0, 0)};
@@ -262,25 +272,32 @@ tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, Networ
   }
 
   // --- batch and trajectory labels, projection leaves
-  for (int j = 0; j < batch_log2; ++j) net.batch_labels.push_back(next_label++);
+  for (int j = 0; j < batch_log2; ++j) net.batch_labels.push_back(new_label(-1, -1));
   if (net.noisy)
-    for (int j = 0; j < traj_log2; ++j) net.traj_labels.push_back(next_label++);
+    for (int j = 0; j < traj_log2; ++j) net.traj_labels.push_back(new_label(-1, -1));
   for (auto& L : leaves)
     if (L.kind == LEAF_TRAJ)
       for (int l : net.traj_labels) L.labels.push_back(l);
   for (int q = 0; q < n; ++q) {
+    if (q < (int)open.size() && open[q]) {
+      net.open_qubits.push_back(q);
+      net.open_labels.push_back(final_label[q]);
+      continue;
+    }
     Leaf P;
     P.kind = LEAF_PROJ;
     P.qubit = q;
     P.labels = {final_label[q]};
     for (int l : net.batch_labels) P.labels.push_back(l);
     leaves.push_back(P);
+    net.proj_src.push_back(q % net.row_len);
   }
   net.leaves = std::move(leaves);
   net.n_labels = next_label;
   net.is_output.assign(next_label, 0);
   for (int l : net.batch_labels) net.is_output[l] = 1;
   for (int l : net.traj_labels) net.is_output[l] = 1;
+  for (int l : net.open_labels) net.is_output[l] = 1;
   return TNQ_OK;
 }
 

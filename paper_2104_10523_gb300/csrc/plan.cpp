@@ -233,11 +233,13 @@ void layout_steps(Plan* p) {
   off = align_up(off + 8 * p->traj_cumq.size(), 256);
   p->ws_misc = off;
   const size_t per = size_t(1) << p->batch_log2;
+  const size_t n_open = p->net.open_qubits.size();
   p->ws_bits = off + 256;
-  p->ws_out_stage = align_up(p->ws_bits + size_t(p->net.n_qubits) * per, 256);
-  p->ws_psum = align_up(p->ws_out_stage + 16 * per, 256);
+  p->ws_out_stage = align_up(p->ws_bits + size_t(p->net.row_len) * per, 256);
+  p->ws_psum = align_up(p->ws_out_stage + ((16 * per) << n_open), 256);
   p->ws_p2sum = align_up(p->ws_psum + 8 * per, 256);
-  off = align_up(p->ws_p2sum + 8 * per, 256);
+  p->ws_qtab = align_up(p->ws_p2sum + 8 * per, 256);
+  off = align_up(p->ws_qtab + 4 * (p->net.proj_src.size() + n_open), 256);
   p->ws_total = off;
 }
 
@@ -338,9 +340,12 @@ void step_features(const Plan& p, int precision, std::vector<float>* out) {
   }
 }
 
-tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p) { return make_plan_ranked(c, o, p, nullptr); }
+tnq_status make_plan(const Circuit& c, const tnq_plan_opts& o, Plan* p, const NetworkSpec& spec) {
+  return make_plan_ranked(c, o, p, nullptr, spec);
+}
 
-tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, const CandidateRanker* ranker) {
+tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, const CandidateRanker* ranker,
+                            const NetworkSpec& spec) {
   auto t0 = std::chrono::steady_clock::now();
   if (o.batch_log2 < 0 || o.batch_log2 > 16 || o.traj_log2 < 0 || o.traj_log2 > 16)
     return fail(TNQ_ERR_INVALID_ARG, "batch_log2/traj_log2 must be in [0, 16]");
@@ -348,7 +353,7 @@ tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, c
     return fail(TNQ_ERR_INVALID_ARG, "max_intermediate_log2 must be in [1, 31]");
   p->batch_log2 = o.batch_log2;
   p->traj_log2 = c.n_channels > 0 ? o.traj_log2 : 0;
-  tnq_status st = build_network(c, p->batch_log2, p->traj_log2, &p->net);
+  tnq_status st = build_network(c, p->batch_log2, p->traj_log2, spec.open, spec.row_len, &p->net);
   if (st != TNQ_OK) return st;
   p->hyper = make_hyper(p->net);
   build_traj_program(c, p);

@@ -25,6 +25,7 @@ TNQ_ERR_NO_DEVICE = 7
 TNQ_PREC_FP32, TNQ_PREC_TF32, TNQ_PREC_TF32X3, TNQ_PREC_BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3}
 TNQ_PATH_GREEDY, TNQ_PATH_BISECT, TNQ_PATH_BEST, TNQ_PATH_LEARNED = 0, 1, 2, 3
+TNQ_KERNELS_DEFAULT, TNQ_KERNELS_TENSOR_CORES = 0, 1
 
 # Every exported symbol of include/tnq.h (checked by the CPU tests).
 EXPORTS = (
@@ -40,6 +41,8 @@ EXPORTS = (
     "tnq_cost_model_n_params", "tnq_cost_model_bind", "tnq_cost_model_set_params", "tnq_cost_model_get_params",
     "tnq_cost_model_gradients", "tnq_cost_model_train", "tnq_cost_model_predict", "tnq_plan_step_features",
     "tnq_plan_create_learned", "tnq_plan_get_candidates", "tnq_plan_autotune", "tnq_amplitudes_slices",
+    "tnq_plan_get_tree", "tnq_plan_get_leaf_wires", "tnq_ctx_set_kernel_policy", "tnq_plan_create_open",
+    "tnq_plan_create_density", "tnq_density_probabilities",
 )
 
 
@@ -56,7 +59,7 @@ class TnqPlanInfo(C.Structure):
     _fields_ = [("n_leaves", C.c_int), ("n_steps", C.c_int), ("n_sliced", C.c_int), ("max_log2", C.c_int),
                 ("batch_log2", C.c_int), ("traj_log2", C.c_int), ("flops_per_pass", C.c_double),
                 ("flops_per_batch", C.c_double), ("bytes_per_pass", C.c_double), ("search_ms", C.c_double),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("n_open", C.c_int)]
 
 
 class TnqError(RuntimeError):
@@ -126,6 +129,12 @@ def load() -> C.CDLL:
         "tnq_plan_get_candidates": ([vp, dp, dp, i32, ip, ip, ip], i32),
         "tnq_plan_autotune": ([vp, vp, i32, ip, ip], i32),
         "tnq_amplitudes_slices": ([vp, vp, i64, vp, i64, i64, vp], i32),
+        "tnq_plan_get_tree": ([vp, ip], i32),
+        "tnq_plan_get_leaf_wires": ([vp, i32, i32, ip, ip], i32),
+        "tnq_ctx_set_kernel_policy": ([vp, i32], i32),
+        "tnq_plan_create_open": ([vp, C.POINTER(TnqPlanOpts), i32, ip, C.POINTER(vp)], i32),
+        "tnq_plan_create_density": ([vp, C.POINTER(TnqPlanOpts), C.POINTER(vp)], i32),
+        "tnq_density_probabilities": ([vp, vp, i64, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -188,6 +197,27 @@ def tnq_plan_create(circ_h, max_intermediate_log2=28, batch_log2=0, traj_log2=0,
     return h
 
 
+def tnq_plan_create_open(circ_h, open_qubits, max_intermediate_log2=28, batch_log2=0, traj_log2=0,
+                         path_mode=TNQ_PATH_BEST, n_candidates=16, seed=0):
+    o = TnqPlanOpts(max_intermediate_log2, batch_log2, traj_log2, path_mode, n_candidates, seed)
+    h = C.c_void_p()
+    check(load().tnq_plan_create_open(circ_h, C.byref(o), len(open_qubits), _int_array(open_qubits), C.byref(h)))
+    return h
+
+
+def tnq_plan_create_density(circ_h, max_intermediate_log2=28, batch_log2=0, path_mode=TNQ_PATH_BEST,
+                            n_candidates=16, seed=0):
+    o = TnqPlanOpts(max_intermediate_log2, batch_log2, 0, path_mode, n_candidates, seed)
+    h = C.c_void_p()
+    check(load().tnq_plan_create_density(circ_h, C.byref(o), C.byref(h)))
+    return h
+
+
+def tnq_density_probabilities(ctx, plan, bits, p_out):
+    """bits: int8 [n_bs][n] (host or device); p_out: float64 [n_bs] (same choices)."""
+    check(load().tnq_density_probabilities(ctx, plan, int(bits.shape[0]), _ptr(bits), _ptr(p_out)))
+
+
 def tnq_plan_destroy(h):
     load().tnq_plan_destroy(h)
 
@@ -202,6 +232,22 @@ def tnq_plan_get_steps(h, n_steps) -> np.ndarray:
     rec = np.zeros(8 * n_steps, dtype=np.int32)
     check(load().tnq_plan_get_steps(h, rec.ctypes.data_as(C.POINTER(C.c_int))))
     return rec.reshape(n_steps, 8)
+
+
+def tnq_plan_get_tree(h, n_steps) -> np.ndarray:
+    """[n_steps][2] tensor ids contracted by each step (leaves first, then step results)."""
+    pairs = np.zeros(2 * max(n_steps, 1), dtype=np.int32)
+    check(load().tnq_plan_get_tree(h, pairs.ctypes.data_as(C.POINTER(C.c_int))))
+    return pairs[:2 * n_steps].reshape(n_steps, 2)
+
+
+def tnq_plan_get_leaf_wires(h, leaf) -> list:
+    """[(qubit, position), ...] of the leaf's indices ((-1, -1) = batch/trajectory index)."""
+    n = C.c_int()
+    check(load().tnq_plan_get_leaf_wires(h, int(leaf), 0, None, C.byref(n)))
+    w = np.zeros(2 * max(n.value, 1), dtype=np.int32)
+    check(load().tnq_plan_get_leaf_wires(h, int(leaf), n.value, w.ctypes.data_as(C.POINTER(C.c_int)), C.byref(n)))
+    return [(int(w[2 * j]), int(w[2 * j + 1])) for j in range(n.value)]
 
 
 def tnq_ctx_create(device=0, stream=None, precision=TNQ_PREC_FP32):
@@ -271,6 +317,10 @@ def tnq_plan_autotune(ctx, plan, reps=3):
 
 def tnq_ctx_set_graphs(ctx, enable: bool):
     check(load().tnq_ctx_set_graphs(ctx, 1 if enable else 0))
+
+
+def tnq_ctx_set_kernel_policy(ctx, policy: int):
+    check(load().tnq_ctx_set_kernel_policy(ctx, int(policy)))
 
 
 def tnq_ctx_launch_count(ctx) -> int:
@@ -400,9 +450,14 @@ class Circuit:
 class Plan:
     """Owns a tnq_plan; info() and steps() describe it."""
 
-    def __init__(self, circuit: Circuit, **opts):
+    def __init__(self, circuit: Circuit, open_qubits=None, density=False, **opts):
         self.circuit = circuit
-        self.h = tnq_plan_create(circuit.h, **opts)
+        if density:
+            self.h = tnq_plan_create_density(circuit.h, **opts)
+        elif open_qubits:
+            self.h = tnq_plan_create_open(circuit.h, list(open_qubits), **opts)
+        else:
+            self.h = tnq_plan_create(circuit.h, **opts)
         self.info = tnq_plan_get_info(self.h)
         self.workspace = None
 
@@ -424,6 +479,12 @@ class Plan:
 
     def candidates(self):
         return tnq_plan_get_candidates(self.h)
+
+    def tree(self):
+        return tnq_plan_get_tree(self.h, self.info["n_steps"])
+
+    def leaf_wires(self):
+        return [tnq_plan_get_leaf_wires(self.h, i) for i in range(self.info["n_leaves"])]
 
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:
@@ -451,16 +512,26 @@ class Context:
         tnq_plan_bind(self.h, plan.h, plan.workspace, nbytes)
 
     def amplitudes(self, plan: Plan, bits):
-        """complex128 amplitudes; bits: int8 NumPy [n_bs][n] (host) or a torch cuda int8 tensor."""
+        """complex128 amplitudes; bits: int8 NumPy [n_bs][n] (host) or a torch cuda int8 tensor.
+        For a plan with open qubits the result is [n_bs][2^n_open]."""
+        k = plan.info["n_open"]
         if hasattr(bits, "is_cuda") and bits.is_cuda:
             import torch
-            out = torch.empty((bits.shape[0], 2), dtype=torch.float64, device=bits.device)
+            out = torch.empty((bits.shape[0] << k, 2), dtype=torch.float64, device=bits.device)
             tnq_amplitudes(self.h, plan.h, bits, out)
             return out
         b = np.ascontiguousarray(bits, dtype=np.int8)
-        out = np.empty((b.shape[0], 2), dtype=np.float64)
+        out = np.empty((b.shape[0] << k, 2), dtype=np.float64)
         tnq_amplitudes(self.h, plan.h, b, out)
-        return out[:, 0] + 1j * out[:, 1]
+        amp = out[:, 0] + 1j * out[:, 1]
+        return amp.reshape(b.shape[0], 2 ** k) if k else amp
+
+    def density_probabilities(self, plan: Plan, bits):
+        """Exact p(x) (float64 [n_bs]) of a density-matrix plan for host int8 bits [n_bs][n]."""
+        b = np.ascontiguousarray(bits, dtype=np.int8)
+        p = np.empty(b.shape[0], dtype=np.float64)
+        tnq_density_probabilities(self.h, plan.h, b, p)
+        return p
 
     def noisy_probabilities(self, plan: Plan, bits, n_traj, seed):
         """(p, stderr) as float64 arrays for host int8 bits [n_bs][n]."""

@@ -55,14 +55,22 @@ def test_config_small_fp32(T, small_ref, w, mode):
 
 @pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16x3"])
 def test_config_small_tensor_core_modes(T, small_ref, prec):
+    """The small steps of this circuit would stay on the CUDA cores under the
+    default rule; the tensor-core policy moves every step a tensor-core kernel
+    accepts onto it, and the timing records show which kernels ran."""
     c, ref = small_ref
     ctx = T.Context(0, prec)
-    ctx_set = ctx  # the small steps of this circuit would all stay on the CUDA cores; force the tensor cores
     plan = T.Plan(T.Circuit(c), batch_log2=6, path_mode=2, n_candidates=4, seed=1)
     ctx.bind(plan)
-    T.tnq_ctx_set_timing(ctx_set.h, True)
+    T.tnq_ctx_set_kernel_policy(ctx.h, T.TNQ_KERNELS_TENSOR_CORES)
+    T.tnq_ctx_set_timing(ctx.h, True)
     amp = ctx.amplitudes(plan, CONFIG_SMALL_BITS)
+    kinds = T.tnq_ctx_get_timings(ctx.h)[:, 0].astype(int)
+    assert (kinds == 2).sum() + (kinds == 5).sum() >= 3, kinds   # general (2) / tall-skinny (5) tcgen05 kernels
     assert rel_l2(amp, ref) <= TOL[prec]
+    # the same policy through the captured graph gives the same amplitudes
+    T.tnq_ctx_set_timing(ctx.h, False)
+    assert np.array_equal(ctx.amplitudes(plan, CONFIG_SMALL_BITS), amp)
 
 
 def test_config_small_matches_tn_oracle(T, small_ref):

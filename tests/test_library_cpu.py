@@ -123,3 +123,81 @@ def test_ctx_create_without_gpu_reports_no_device():
     with pytest.raises(tnq.TnqError) as e:
         tnq.tnq_ctx_create(0, None, tnq.TNQ_PREC_FP32)
     assert e.value.status == tnq.TNQ_ERR_NO_DEVICE
+
+
+@pytest.mark.parametrize("rows,cols,cycles,w", [(3, 4, 8, 0), (3, 4, 8, 2), (4, 4, 10, 0)])
+def test_exported_tree_followed_by_oracle(rows, cols, cycles, w):
+    """tnq_plan_get_tree / tnq_plan_get_leaf_wires describe a valid contraction
+    of the circuit network: the oracle cuts its own network at the exported
+    wires into exactly the plan's groups, follows the tree with its own
+    slicing, and gets the statevector amplitudes."""
+    from oracle import statevector as sv
+    from oracle import tn as otn
+    from workloads import random_bitstrings
+    circ = grid_circuit(rows, cols, cycles, 7)
+    p = _plan(circ, max_intermediate_log2=12, batch_log2=w, path_mode=tnq.TNQ_PATH_BEST, n_candidates=8, seed=2)
+    pairs, gw = p.tree(), p.leaf_wires()
+    assert pairs.shape == (p.info["n_steps"], 2) and len(gw) == p.info["n_leaves"]
+    # every id is used once as an operand; results only after they exist
+    used = sorted(int(x) for x in pairs.ravel())
+    assert used == list(range(p.info["n_leaves"] + p.info["n_steps"] - 1))
+    assert all(max(a, b) < p.info["n_leaves"] + j for j, (a, b) in enumerate(pairs))
+    # batch labels appear as (-1, -1) on projection leaves only
+    assert sum(1 for g in gw for q, _ in g if q < 0) == circ.n * w
+    bits = random_bitstrings(circ.n, 3, 11)
+    ref = sv.amplitudes(circ, bits)
+    for b, want in zip(bits, ref):
+        net, wires = otn.build_network_wires(circ, b)
+        order = otn.order_from_groups(net, wires, gw, pairs)
+        sl = otn.choose_slices(net, order, 7)
+        got = complex(np.asarray(otn.contract_sliced(net, sl, order)).reshape(()))
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+
+
+def test_leaf_wires_rejects_bad_leaf():
+    p = _plan(grid_circuit(2, 2, 2, 1))
+    with pytest.raises(tnq.TnqError):
+        tnq.tnq_plan_get_leaf_wires(p.h, p.info["n_leaves"])
+
+
+def test_stored_config3_tree_matches_oracle_network():
+    """The stored tree of the benchmark circuit partitions the oracle's own
+    network (every group found, nothing left over) for a few bitstrings."""
+    from oracle import golden
+    from oracle import tn as otn
+    from workloads import random_bitstrings
+    circ = grid_circuit(6, 6, 14, 2104)
+    gw, pairs = golden.read_tree(os.path.join(ROOT, "tests", "golden", "config3_order.txt"))
+    for b in random_bitstrings(36, 1024, 10523)[:3]:
+        net, wires = otn.build_network_wires(circ, b)
+        order = otn.order_from_groups(net, wires, gw, pairs)
+        assert len(order) == len(net) - 1
+        flops, mx = otn.order_cost(otn.fix_labels(net, {l: 0 for l in otn.choose_slices(net, order, 24)}), order)
+        assert mx <= 24 and flops < 1e11
+
+
+def test_kernel_policy_validation():
+    """Only the two documented kernel policies are accepted (checked before any
+    device work, so this runs without a GPU)."""
+    L = tnq.load()
+    assert L.tnq_ctx_set_kernel_policy(None, 1) == tnq.TNQ_ERR_INVALID_ARG
+
+
+def test_open_plan_validation():
+    c = tnq.Circuit(grid_circuit(3, 4, 8, 1))
+    for bad in ([12], [3, 3], [-1]):
+        with pytest.raises(tnq.TnqError) as e:
+            tnq.Plan(c, open_qubits=bad)
+        assert e.value.status == tnq.TNQ_ERR_INVALID_ARG
+    with pytest.raises(tnq.TnqError) as e:
+        tnq.Plan(c, open_qubits=list(range(6)), max_intermediate_log2=5)
+    assert e.value.status == tnq.TNQ_ERR_PLAN_INFEASIBLE
+    p = tnq.Plan(c, open_qubits=[1, 6], batch_log2=2)
+    assert p.info["n_open"] == 2
+    # the root keeps the batch and open indices; no projection leaf for open qubits
+    assert p.steps()[-1][2] == 4
+    assert sum(1 for g in p.leaf_wires() if len(g) == 3 and g[1] == (-1, -1)) == 10
+    noisy = tnq.Circuit(noisy_grid_circuit(2, 2, 2, 1, 1e-3, 1e-3))
+    with pytest.raises(tnq.TnqError) as e:
+        tnq.Plan(noisy, open_qubits=[0])
+    assert e.value.status == tnq.TNQ_ERR_NOT_SUPPORTED
