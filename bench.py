@@ -48,10 +48,14 @@ def parse():
     ap.add_argument("--candidates", type=int, default=2048)
     ap.add_argument("--cap", type=int, default=28)
     ap.add_argument("--skip-fp32", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="circuit", choices=["circuit", "pair"],
                     help="circuit: 6x6 amplitude workload; pair: one pairwise contraction (microbenchmark)")
     ap.add_argument("--mnk", default="12,12,12", help="pair workload: log2 of M, N, K")
+    ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-min-slices", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--dump-amplitudes", default=None,
+                    help="write the accuracy pass's amplitudes (every mode) to this JSON file")
     return ap.parse_args()
 
 
@@ -121,39 +125,71 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
-def oracle_sample(plan_steps, flops_per_amp, seconds):
-    """Time the oracle's FP64 pairwise contraction (oracle.tn.contract_pair) on
-    random tensors with the plan's step shapes (operands <= 2^22 elements),
-    for about `seconds`; return (amplitudes/s, cores, description)."""
-    import numpy as np
-    from oracle import tn as otn
-    rng = np.random.default_rng(0)
-    shapes = [r for r in plan_steps if max(r[0], r[1]) <= 22]
-    shapes.sort(key=lambda r: -(r[3] + r[4] + r[5] + r[6]))
-    done_flops, t0, n = 0.0, time.perf_counter(), 0
-    while time.perf_counter() - t0 < seconds and shapes:
-        r = shapes[n % len(shapes)]
-        nh, nm, nn, nk = int(r[3]), int(r[4]), int(r[5]), int(r[6])
-        lab_k = list(range(nk))
-        lab_m = list(range(100, 100 + nm))
-        lab_n = list(range(200, 200 + nn))
-        a_lab = lab_k + lab_m
-        b_lab = lab_k + lab_n
-        for h in range(2 ** nh):  # batch labels: one contraction per batch entry
-            A = rng.standard_normal((2,) * len(a_lab)) + 1j * rng.standard_normal((2,) * len(a_lab))
-            B = rng.standard_normal((2,) * len(b_lab)) + 1j * rng.standard_normal((2,) * len(b_lab))
-            otn.contract_pair((A, a_lab), (B, b_lab))
-            done_flops += 8.0 * 2.0 ** (nm + nn + nk)
-            if time.perf_counter() - t0 > seconds:
-                break
-        n += 1
-    dt = time.perf_counter() - t0
-    rate = done_flops / dt
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    desc = (f"oracle FP64 pairwise contraction (np.tensordot) on {n} of the plan's step shapes with operands "
-            f"<= 2^22 elements for {dt:.1f} s: {rate / 1e9:.2f} GFLOP/s, scaled by the plan's "
-            f"{flops_per_amp:.3e} flops per amplitude")
-    return rate / flops_per_amp, cores, desc
+ORDER_FILE = os.path.join(ROOT, "tests", "golden", "config3_order.txt")
+GOLDEN_FILE = os.path.join(ROOT, "tests", "golden", "config3_amplitudes.txt")
+ORACLE_CAP_LOG2 = 24
+
+
+def oracle_slices(seconds, min_slices=1, bitstring=0):
+    """The FP64 oracle (oracle.tn, O2) contracting one amplitude of the
+    workload: its own network for bitstring `bitstring`, the stored contraction
+    tree, its own slicing to <= 2^24-element tensors; slices are contracted one
+    after the other until `seconds` have passed (at least `min_slices`).
+    Returns (slices done, slices per amplitude, seconds)."""
+    import itertools
+    from oracle import golden, tn
+    from workloads import grid_circuit, random_bitstrings
+    circ = grid_circuit(WORKLOAD["rows"], WORKLOAD["cols"], WORKLOAD["cycles"], WORKLOAD["seed"])
+    bits = random_bitstrings(circ.n, WORKLOAD["n_bitstrings"], WORKLOAD["bits_seed"])[bitstring]
+    gw, pairs = golden.read_tree(ORDER_FILE)
+    net, wires = tn.build_network_wires(circ, bits)
+    order = tn.order_from_groups(net, wires, gw, pairs)
+    sl = tn.choose_slices(net, order, ORACLE_CAP_LOG2)
+    t0 = time.perf_counter()
+    done = 0
+    for vals in itertools.product((0, 1), repeat=len(sl)):
+        tn.contract(tn.fix_labels(net, dict(zip(sl, vals))), order)
+        done += 1
+        if done >= min_slices and time.perf_counter() - t0 >= seconds:
+            break
+    return done, 2 ** len(sl), time.perf_counter() - t0
+
+
+def oracle_sample_subprocess(threads, seconds, min_slices=1):
+    """Run oracle_slices in a fresh interpreter whose BLAS uses `threads` threads."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(seconds), "--oracle-min-slices",
+           str(min_slices)]
+    res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=3600)
+    if res.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {res.stderr[-2000:]}")
+    done, per_amp, dt = json.loads(res.stdout.strip().splitlines()[-1])
+    return done, per_amp, dt
+
+
+def cpu_baseline(seconds):
+    """The oracle timed on the host cores: all cores, then one thread."""
+    cores = os.cpu_count() or 1
+    done, per_amp, dt = oracle_sample_subprocess(cores, seconds)
+    d1, _, t1 = oracle_sample_subprocess(1, seconds)
+    rate = done / per_amp / dt
+    rate1 = d1 / per_amp / t1
+    desc = (f"oracle O2 (FP64, np.tensordot) contracting amplitude 0 of the workload along the stored tree "
+            f"(tests/golden/config3_order.txt), sliced by the oracle into {per_amp} slices of <= "
+            f"2^{ORACLE_CAP_LOG2} elements: {done} slices in {dt:.1f} s on {cores} threads, scaled to "
+            f"amplitudes/s; one thread: {d1} slices in {t1:.1f} s = {rate1:.3e} amplitudes/s")
+    return {"value": rate, "unit": "amplitudes/s", "cores": cores, "kind": "oracle", "sample": desc,
+            "single_thread_value": rate1}
+
+
+def golden_amplitudes():
+    """(indices, FP64 amplitudes) stored by the oracle for this workload, or (None, None)."""
+    if not os.path.exists(GOLDEN_FILE):
+        return None, None
+    from oracle import golden
+    return golden.read_amplitudes(GOLDEN_FILE)
 
 
 # ---------------------------------------------------------------- main
@@ -163,6 +199,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if a.oracle_sample is not None:
+        print(json.dumps(oracle_slices(a.oracle_sample, a.oracle_min_slices)), flush=True)
+        return
     if a.impl == "reference":
         return run_reference(a, world, rank)
     if a.workload == "pair":
@@ -237,7 +276,6 @@ def main():
     value = amps / elapsed
     flops_step = info["flops_per_batch"]
     tflops = flops_step * a.steps * world / elapsed / 1e12
-    mixed_amp = out.cpu().numpy()
 
     log(f"timed steps: {elapsed:.3f} s")
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
@@ -266,24 +304,58 @@ def main():
     roofline, kernel_share = roofline_of(rec, a.precision)
 
     log("roofline pass done")
-    # ---- plain FP32 arm on the same plan and the same batch
+    # ---- accuracy against the FP64 oracle on the stored bitstrings (same plan, same
+    # kernels), and the plain FP32 arm: speed on the timed batches, accuracy on the stored ones
+    gidx, gref = golden_amplitudes()
+    if gidx is None:
+        gidx = np.arange(4 * B)
+    acc_bits = bits_all[gidx]
+    dump = {"bitstring_indices": [int(i) for i in gidx]}
+
+    def amps_of(c):
+        o = np.empty((acc_bits.shape[0], 2))
+        tnq.tnq_amplitudes(c.h, plan.h, np.ascontiguousarray(acc_bits), o)
+        return o[:, 0] + 1j * o[:, 1]
+
+    def err_of(amp):
+        if gref is None:
+            return None
+        return float(np.linalg.norm(amp - gref) / np.linalg.norm(gref))
+
+    mode_amp = amps_of(ctx)
+    dump[a.precision] = [[z.real, z.imag] for z in mode_amp]
+    accuracy = {"rel_l2_vs_fp64": err_of(mode_amp), "bitstrings": int(acc_bits.shape[0]),
+                "reference": "FP64 oracle O2 amplitudes (tests/golden/config3_amplitudes.txt)"
+                if gref is not None else "unavailable (no stored FP64 amplitudes)",
+                "tolerance": 1e-5}
     compare = None
     if not a.skip_fp32:
         ctx32 = tnq.Context(local, "fp32")
         ctx32.bind(plan)
         last = a.warmup + a.steps - 1
-        tnq.tnq_amplitudes(ctx32.h, plan.h, dev_bits[last], out)  # warm
+        tnq.tnq_amplitudes(ctx32.h, plan.h, dev_bits[last], out)  # warm (captures the FP32 graph)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
         e0.record(stream)
-        tnq.tnq_amplitudes(ctx32.h, plan.h, dev_bits[last], out)
+        for _ in range(reps):
+            tnq.tnq_amplitudes(ctx32.h, plan.h, dev_bits[last], out)
         e1.record(stream)
         torch.cuda.synchronize()
-        t32 = e0.elapsed_time(e1) / 1e3
-        fp32_amp = out.cpu().numpy()
-        diff = np.linalg.norm(mixed_amp - fp32_amp) / np.linalg.norm(fp32_amp)
+        t32 = e0.elapsed_time(e1) / 1e3 / reps
+        fp32_amp = amps_of(ctx32)
+        dump["fp32"] = [[z.real, z.imag] for z in fp32_amp]
         compare = {"fp32_value": B / t32, "fp32_tflops": flops_step / t32 / 1e12,
-                   "speedup_vs_fp32": value / world / (B / t32), "rel_l2_vs_fp32": float(diff)}
+                   "speedup_vs_fp32": value / world / (B / t32),
+                   "fp32_rel_l2_vs_fp64": err_of(fp32_amp),
+                   "rel_l2_vs_fp32": float(np.linalg.norm(mode_amp - fp32_amp) / np.linalg.norm(fp32_amp))}
+        del ctx32
+    accuracy["meets_tolerance"] = (accuracy["rel_l2_vs_fp64"] is not None and
+                                   accuracy["rel_l2_vs_fp64"] <= accuracy["tolerance"])
+    if a.dump_amplitudes and rank == 0:
+        with open(a.dump_amplitudes, "w") as f:
+            json.dump(dump, f)
+    log("accuracy pass and fp32 arm done")
 
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": a.steps,
@@ -295,6 +367,7 @@ def main():
                    "autotuned_steps": {"tensor_core": n_tc, "cuda_core": n_cc}, "l2": "working set larger than L2 (intermediates up to "
                    f"2^{info['max_log2']} x 8 B)", "parallelism": f"dp{world} (independent bitstrings)"},
         "contraction_tflops": tflops,
+        "accuracy": accuracy,
         "roofline": roofline,
         "kernel_share": kernel_share,
         "e2e": e2e,
@@ -302,11 +375,9 @@ def main():
         "clocks": clocks.summary(),
         "compare": compare,
     }
-    log("fp32 arm done")
     if rank == 0:
-        rate, cores, desc = oracle_sample(plan.steps().tolist(), flops_step / B, a.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
-                                "sample": desc}
+        line["cpu_baseline"] = cpu_baseline(a.cpu_seconds)
+        log("cpu baseline done")
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -443,32 +514,28 @@ def run_pair(a, local, rank):
 
 
 def run_reference(a, world, rank):
-    """The oracle on the host cores, same workload, metric and unit; bounded sample per step."""
+    """The oracle on the host cores, same workload, metric and unit.  One step
+    is one slice of one amplitude contracted by the FP64 oracle (O2) along the
+    stored tree, sliced by the oracle itself; amplitudes/s = slices done /
+    slices per amplitude / seconds."""
     if rank != 0:
         return
-    from paper_2104_10523_gb300 import build, tnq
-    from workloads import grid_circuit
-    build.build()
-    tnq.load()
-    circ = grid_circuit(WORKLOAD["rows"], WORKLOAD["cols"], WORKLOAD["cycles"], WORKLOAD["seed"])
-    B = 2 ** a.batch_log2
-    plan = tnq.Plan(tnq.Circuit(circ), max_intermediate_log2=a.cap, batch_log2=a.batch_log2,
-                    path_mode=tnq.TNQ_PATH_BEST, n_candidates=a.candidates, seed=7)
-    steps = plan.steps().tolist()
-    per_amp = plan.info["flops_per_batch"] / B
-    per_step = max(2.0, min(a.cpu_seconds, 120.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
-        oracle_sample(steps, per_amp, per_step / 4)
-    rates = []
-    desc, cores = "", 1
-    for _ in range(a.steps):
-        r, cores, desc = oracle_sample(steps, per_amp, per_step)
-        rates.append(r)
-    value = statistics.mean(rates)
+        oracle_slices(0.0, 1)
+    times, per_amp = [], 1
+    for i in range(a.steps):
+        done, per_amp, dt = oracle_slices(0.0, 1)
+        times.append(dt / done)
+    t_slice = statistics.mean(times)
+    value = 1.0 / per_amp / t_slice
+    cores = os.cpu_count() or 1
+    desc = (f"oracle O2 (FP64, np.tensordot, BLAS threads = {os.environ.get('OPENBLAS_NUM_THREADS', 'default')}) "
+            f"contracting amplitude 0 of the workload along tests/golden/config3_order.txt, one of its {per_amp} "
+            f"slices (<= 2^{ORACLE_CAP_LOG2} elements) per step, {t_slice:.2f} s per slice")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": B / value * 1e3, "higher_is_better": True,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_slice * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(a), "bitstrings_per_step": B},
+            "config": {"workload": workload_desc(a), "step": f"one of the {per_amp} slices of one amplitude"},
             "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
