@@ -100,3 +100,25 @@ def wavefunction_slice(circ, bitstrings) -> np.ndarray:
         idx = tuple(slice(None) if v == -1 else int(v) for v in b)
         rows.append(np.ascontiguousarray(psi[idx]).reshape(-1))
     return np.array(rows, dtype=np.complex128)
+
+
+PAULI = {"I": np.eye(2, dtype=np.complex128),
+         "X": np.array([[0, 1], [1, 0]], dtype=np.complex128),
+         "Y": np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+         "Z": np.array([[1, 0], [0, -1]], dtype=np.complex128)}
+
+
+def expectation(circ, paulis, coeffs):
+    """<psi|H|psi> (Eq. exp_val) for |psi> = U|0...0> and H = sum_t c_t P_t,
+    P_t given as a string over IXYZ (character q acts on qubit q).  Returns
+    (value, per-term <psi|P_t|psi>)."""
+    psi = final_state(circ)
+    vals = []
+    for ps in paulis:
+        phi = psi
+        for q, ch in enumerate(ps):
+            if ch != "I":
+                phi = apply_matrix(phi, PAULI[ch], [q])
+        vals.append(np.vdot(psi, phi))
+    vals = np.array(vals)
+    return complex(np.dot(coeffs, vals)), vals

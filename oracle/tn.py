@@ -398,3 +398,36 @@ def density_probability(circ, bitstring, order=None) -> float:
     net, _ = build_density_network_wires(circ, bitstring)
     val = contract(net, order)[0]
     return float(np.real(np.asarray(val).reshape(())))
+
+
+_PAULI = {"I": np.eye(2, dtype=np.complex128),
+          "X": np.array([[0, 1], [1, 0]], dtype=np.complex128),
+          "Y": np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+          "Z": np.array([[1, 0], [0, -1]], dtype=np.complex128)}
+
+
+def build_expectation_network(circ, pauli_string) -> List[Tensor]:
+    """The double-depth network of Fig. 3 for <psi|P|psi>: the circuit's
+    network U|0...0> with its final legs open, one Pauli tensor per qubit on
+    them, then the conjugate network (every tensor of U|0...0> complex
+    conjugated, its output legs joined to the Pauli tensors)."""
+    ket = build_network(circ)
+    ket_open = list(build_network.last_open)
+    shift = 1 + max(l for _, ls in ket for l in ls)
+    bra = [(np.conj(T), [l + shift for l in ls]) for T, ls in ket]
+    tensors = list(ket) + bra
+    for q, ch in enumerate(pauli_string):
+        # P[out, in]: in = the ket's final leg, out = the bra's final leg
+        tensors.append((_PAULI[ch], [ket_open[q] + shift, ket_open[q]]))
+    return tensors
+
+
+def expectation(circ, paulis, coeffs, order: str = "greedy", seed: int = 0):
+    """(value, per-term values) of <psi|H|psi> through the double-depth network."""
+    vals = []
+    for ps in paulis:
+        net = build_expectation_network(circ, ps)
+        o = greedy_order(net) if order == "greedy" else random_order(net, seed)
+        vals.append(complex(np.asarray(contract(net, o)[0]).reshape(())))
+    vals = np.array(vals)
+    return complex(np.dot(coeffs, vals)), vals

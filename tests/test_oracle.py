@@ -214,6 +214,41 @@ def test_wavefunction_slice_both_oracles_and_norm():
     assert abs(s1[17][y] - sv.amplitudes(c, [full])[0]) < 1e-15
 
 
+def test_expectation_closed_forms():
+    """Sec. 3.1.2, Eq. exp_val.  Cat state (H then CX chain): <Z_0 Z_k> = 1,
+    <X...X> = 1, <Z_0> = 0, <Y_0 Y_1 X_2...X_{n-1}> = -1 (two Y's on a cat
+    state give i*i = -1); X on qubit 0 of |0>: <Z_0> = -1.  Both oracles."""
+    n = 6
+    c = ghz_circuit(n)
+    terms = ["ZIIIIZ", "XXXXXX", "ZIIIII", "YYXXXX", "IIIIII"]
+    want = np.array([1.0, 1.0, 0.0, -1.0, 1.0])
+    coeffs = np.array([0.5, -2.0, 3.0, 1.5, 0.25])
+    for fn in (sv.expectation, tn.expectation):
+        v, per = fn(c, terms, coeffs)
+        assert np.allclose(per, want, atol=1e-14)
+        assert abs(v - np.dot(coeffs, want)) < 1e-13
+    v, per = tn.expectation(Circuit(2).gate(X, 0), ["ZI", "IZ"], [1.0, 1.0])
+    assert np.allclose(per, [-1.0, 1.0], atol=1e-15)
+
+
+def test_expectation_both_oracles_random_circuit():
+    """O1 (Pauli strings applied to the statevector) and O2 (the double-depth
+    network of Fig. 3, random order) agree; every term is real (P Hermitian),
+    and the sum over all 4^n Pauli strings of <P>^2 equals 2^n for a pure
+    state (purity)."""
+    c = grid_circuit(2, 2, 4, 17)
+    rng = np.random.default_rng(3)
+    terms = ["".join(rng.choice(list("IXYZ"), size=4)) for _ in range(12)]
+    coeffs = rng.standard_normal(12)
+    v1, p1 = sv.expectation(c, terms, coeffs)
+    v2, p2 = tn.expectation(c, terms, coeffs, order="random", seed=5)
+    assert np.allclose(p1, p2, atol=1e-14)
+    assert np.allclose(np.imag(p1), 0, atol=1e-15)
+    allp = ["".join(t) for t in itertools.product("IXYZ", repeat=4)]
+    _, pa = sv.expectation(c, allp, np.zeros(len(allp)))
+    assert abs(np.sum(np.abs(pa) ** 2) - 16.0) < 1e-12
+
+
 def test_norm_statevector_config_small():
     c = grid_circuit(3, 4, 8, 1234)
     psi = sv.final_state(c)
