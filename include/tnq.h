@@ -164,6 +164,22 @@ tnq_status tnq_plan_create_open(const tnq_circuit* c, const tnq_plan_opts* opts,
  * tnq_plan_create; NOT_SUPPORTED for a channel on two qubits; INVALID_ARG when
  * 2n exceeds 4096. */
 tnq_status tnq_plan_create_density(const tnq_circuit* c, const tnq_plan_opts* opts, tnq_plan** out);
+/* Expectation values <psi|H|psi> (Sec. 3.1.2, Eq. exp_val) of an observable
+ * H = sum_t c_t P_t, P_t a product of Paulis, for |psi> = U|0...0>, by the
+ * conjugate network of Fig. 3: the circuit's network, the Pauli tensors of a
+ * term on the open legs, then the conjugate network, closed by <0...0|; the
+ * value of that network is <0|U^dagger P_t U|0>.  Gates outside the backward
+ * light cone of the observable's support cancel against their conjugates and
+ * are left out (the simplification the paper notes for sparse observables).
+ * The Pauli tensors of one qubit form an index over terms, so 2^traj_log2
+ * terms are contracted together per pass, sharing the rest of the network.
+ * paulis: host, [n_terms][n_qubits] chars from "IXYZ" (row t is term t,
+ * entry q acts on qubit q), copied.  opts as tnq_plan_create; batch_log2 is
+ * ignored, traj_log2 sets the terms per pass (at most those needed).
+ * Errors: INVALID_ARG (n_terms outside [1, 2^24], another character),
+ * NOT_SUPPORTED (circuit with channels), PLAN_INFEASIBLE as tnq_plan_create. */
+tnq_status tnq_plan_create_expectation(const tnq_circuit* c, const tnq_plan_opts* opts, int64_t n_terms,
+                                       const char* paulis, tnq_plan** out);
 void tnq_plan_destroy(tnq_plan* p);
 tnq_status tnq_plan_get_info(const tnq_plan* p, tnq_plan_info* info);
 /* Per-step shape record: for step i, writes 8 ints
@@ -234,6 +250,14 @@ tnq_status tnq_amplitudes_slices(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const 
  * dropped.  Errors: INVALID_ARG (not a density-matrix plan, bit not 0/1),
  * WORKSPACE, CUDA. */
 tnq_status tnq_density_probabilities(tnq_ctx* ctx, tnq_plan* p, int64_t n_bs, const int8_t* bits, double* p_out);
+
+/* Evaluate an expectation-value plan (tnq_plan_create_expectation):
+ * *value = sum_t coeffs[t] * <psi|P_t|psi>, summed in FP64 in term order.
+ * coeffs: host, [n_terms] real coefficients; term_values: host [n_terms] or
+ * NULL, receives each <psi|P_t|psi> (real for Hermitian P_t; the rounding
+ * imaginary part is dropped).  Errors: INVALID_ARG (not an expectation plan,
+ * NULL coeffs or value), WORKSPACE, CUDA, TIMEOUT. */
+tnq_status tnq_expectation(tnq_ctx* ctx, tnq_plan* p, const double* coeffs, double* value, double* term_values);
 
 /* Noisy probabilities p(x) = <x|rho|x> estimated from n_traj stochastic
  * trajectories (Eq. kraus_sum channels, one Kraus operator drawn per channel

@@ -236,6 +236,115 @@ tnq_status tnq_plan_create_density(const tnq_circuit* c, const tnq_plan_opts* op
   return TNQ_OK;
 }
 
+tnq_status tnq_plan_create_expectation(const tnq_circuit* c, const tnq_plan_opts* opts, int64_t n_terms,
+                                       const char* paulis, tnq_plan** out) {
+  if (!c || !opts || !out || (n_terms > 0 && !paulis)) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  if (n_terms < 1 || n_terms > (int64_t(1) << 24)) return fail(TNQ_ERR_INVALID_ARG, "n_terms must be in [1, 2^24]");
+  if (c->c.n_channels > 0) return fail(TNQ_ERR_NOT_SUPPORTED, "expectation values of a circuit with channels");
+  const int n = c->c.n;
+  // support of the observable: qubits where some term is not the identity
+  std::vector<char> supp(n, 0);
+  for (int64_t t = 0; t < n_terms; ++t)
+    for (int q = 0; q < n; ++q) {
+      const char ch = paulis[t * n + q];
+      if (ch != 'I' && ch != 'X' && ch != 'Y' && ch != 'Z')
+        return fail(TNQ_ERR_INVALID_ARG, "Pauli strings may hold only I, X, Y, Z");
+      if (ch != 'I') supp[q] = 1;
+    }
+  // Light cone: U^dagger P U with a gate g of U that acts outside the support of
+  // what follows it commutes past P and cancels against g^dagger.  Walking U
+  // backwards, a gate is kept when it touches the current support, which it
+  // then joins.
+  std::vector<char> cone = supp;
+  std::vector<char> keep(c->c.ops.size(), 0);
+  for (int i = (int)c->c.ops.size() - 1; i >= 0; --i) {
+    const COp& op = c->c.ops[i];
+    bool touch = false;
+    for (int q : op.qubits) touch |= cone[q] != 0;
+    if (!touch) continue;
+    keep[i] = 1;
+    for (int q : op.qubits) cone[q] = 1;
+  }
+  Circuit d;
+  d.n = n;
+  int kept = 0;
+  for (size_t i = 0; i < c->c.ops.size(); ++i)
+    if (keep[i]) {
+      d.ops.push_back(c->c.ops[i]);
+      ++kept;
+    }
+  std::vector<int> sel_q;
+  for (int q = 0; q < n; ++q)
+    if (supp[q]) sel_q.push_back(q);
+  const std::vector<cd> I2 = {cd(1, 0), cd(0, 0), cd(0, 0), cd(1, 0)}, X2 = {cd(0, 0), cd(1, 0), cd(1, 0), cd(0, 0)},
+                        Y2 = {cd(0, 0), cd(0, -1), cd(0, 1), cd(0, 0)}, Z2 = {cd(1, 0), cd(0, 0), cd(0, 0), cd(-1, 0)};
+  for (size_t j = 0; j < sel_q.size(); ++j) {
+    COp op;
+    op.channel = true;
+    op.selector = true;
+    op.selector_index = (int)j;
+    op.qubits = {sel_q[j]};
+    op.mats = {I2, X2, Y2, Z2};
+    d.ops.push_back(std::move(op));
+  }
+  d.n_selectors = (int)sel_q.size();
+  // the conjugate network: the kept gates' inverses in reverse order
+  for (int i = (int)c->c.ops.size() - 1; i >= 0; --i) {
+    if (!keep[i]) continue;
+    COp inv = c->c.ops[i];
+    const int D = 1 << (int)inv.qubits.size();
+    std::vector<cd> m(D * D);
+    for (int r = 0; r < D; ++r)
+      for (int k = 0; k < D; ++k) m[r * D + k] = std::conj(inv.mats[0][k * D + r]);
+    inv.mats[0] = m;
+    d.ops.push_back(std::move(inv));
+  }
+  // qubits outside the light cone only contribute <0|0> = 1: renumber the
+  // network's qubits to those that carry an op
+  {
+    std::vector<int> remap(n, -1);
+    int m = 0;
+    for (const COp& op : d.ops)
+      for (int q : op.qubits)
+        if (remap[q] < 0) remap[q] = 0;
+    for (int q = 0; q < n; ++q)
+      if (remap[q] == 0) remap[q] = m++;
+    for (COp& op : d.ops)
+      for (int& q : op.qubits) q = remap[q];
+    d.n = std::max(m, 1);
+  }
+  auto* p = new (std::nothrow) tnq_plan();
+  if (!p) return fail(TNQ_ERR_INVALID_ARG, "out of host memory");
+  Plan& P = p->p;
+  P.expectation = true;
+  P.n_terms = n_terms;
+  P.n_sel = (int)sel_q.size();
+  P.kept_gates = kept;
+  P.picks.resize(size_t(n_terms) * sel_q.size());
+  for (int64_t t = 0; t < n_terms; ++t)
+    for (size_t j = 0; j < sel_q.size(); ++j) {
+      const char ch = paulis[t * n + sel_q[j]];
+      P.picks[size_t(t) * sel_q.size() + j] = int8_t(ch == 'I' ? 0 : ch == 'X' ? 1 : ch == 'Y' ? 2 : 3);
+    }
+  tnq_plan_opts o = *opts;
+  o.batch_log2 = 0;
+  int need = 0;
+  while ((int64_t(1) << need) < n_terms) ++need;
+  o.traj_log2 = std::min(o.traj_log2, need);
+  tnq_status s = make_plan(d, o, &P);
+  if (s != TNQ_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return TNQ_OK;
+}
+
+tnq_status tnq_expectation(tnq_ctx* c, tnq_plan* p, const double* coeffs, double* value, double* term_values) {
+  if (!c || !p) return fail(TNQ_ERR_INVALID_ARG, "NULL argument");
+  return exec_expectation(&c->c, &p->p, coeffs, value, term_values);
+}
+
 void tnq_plan_destroy(tnq_plan* p) {
   if (!p) return;
   plan_release_graph(&p->p);

@@ -556,6 +556,11 @@ tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes) {
                                cudaMemcpyHostToDevice, ctx->stream));
     TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
   }
+  if (!p->picks.empty()) {
+    TNQ_CUDA(cudaMemcpyAsync(base + p->ws_picks, p->picks.data(), p->picks.size(), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
   {
     std::vector<int> tab = p->net.proj_src;
     tab.insert(tab.end(), p->net.open_qubits.begin(), p->net.open_qubits.end());
@@ -576,6 +581,7 @@ tnq_status exec_amplitudes(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, 
 tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* bits, int64_t slice_begin,
                                  int64_t slice_count, double* out) {
   if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
+  if (p->expectation) return fail(TNQ_ERR_INVALID_ARG, "expectation-value plan; use tnq_expectation");
   if (p->net.noisy) return fail(TNQ_ERR_INVALID_ARG, "plan is for a noisy circuit; use tnq_noisy_probabilities");
   if (n_bs < 0 || (n_bs > 0 && (!bits || !out))) return fail(TNQ_ERR_INVALID_ARG, "bad bitstring/output buffers");
   if (n_bs == 0) return TNQ_OK;
@@ -794,7 +800,7 @@ tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, u
 
 tnq_status noisy_checks(Plan* p, int64_t n_traj, int64_t n_bs, const int8_t* bits, const void* out) {
   if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
-  if (!p->net.noisy) return fail(TNQ_ERR_INVALID_ARG, "plan is for a circuit without channels");
+  if (!p->net.noisy || p->expectation) return fail(TNQ_ERR_INVALID_ARG, "plan is for a circuit without channels");
   if (!p->net.open_qubits.empty()) return fail(TNQ_ERR_NOT_SUPPORTED, "noisy plans with open qubits");
   if (n_traj < 1) return fail(TNQ_ERR_INVALID_ARG, "n_traj must be >= 1");
   if (n_bs < 0 || (n_bs > 0 && (!bits || !out))) return fail(TNQ_ERR_INVALID_ARG, "bad bitstring/output buffers");
@@ -874,6 +880,73 @@ tnq_status exec_traj_amplitudes(Ctx* ctx, Plan* p, uint64_t seed, int64_t traj_b
   };
   auto batch_end = [&](int64_t, int64_t) -> tnq_status { return TNQ_OK; };
   return noisy_driver(ctx, p, traj_begin, n_traj, seed, n_bs, bits, consume, batch_end);
+}
+
+tnq_status exec_expectation(Ctx* ctx, Plan* p, const double* coeffs, double* value, double* term_values) {
+  if (!p->bound_ws) return fail(TNQ_ERR_WORKSPACE, "plan has no bound workspace");
+  if (!p->expectation) return fail(TNQ_ERR_INVALID_ARG, "plan is not an expectation-value plan");
+  if (!coeffs || !value) return fail(TNQ_ERR_INVALID_ARG, "NULL coefficients or value");
+  TNQ_CUDA(cudaSetDevice(ctx->device));
+  char* ws = static_cast<char*>(p->bound_ws);
+  int* err_flag = reinterpret_cast<int*>(ws + p->ws_misc);
+  int8_t* bits_stage = reinterpret_cast<int8_t*>(ws + p->ws_bits);
+  double2* stage = reinterpret_cast<double2*>(ws + p->ws_out_stage);
+  const auto& rl = p->tensors[p->root].labels;
+  std::vector<int> tpos;
+  for (int l : p->net.traj_labels) tpos.push_back(int(std::find(rl.begin(), rl.end(), l) - rl.begin()));
+  const int t = (int)tpos.size();
+  const int64_t tper = int64_t(1) << t;
+  const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
+  const int n_slices = 1 << p->slice_labels.size();
+  TNQ_CUDA(cudaMemsetAsync(err_flag, 0, 2 * sizeof(int), ctx->stream));
+  // <0...0| closes every wire (the network is U, the Pauli operators, U^dagger)
+  TNQ_CUDA(cudaMemsetAsync(bits_stage, 0, size_t(p->net.row_len), ctx->stream));
+  TNQ_CUDA(fill_projections(ctx, proj_leaves(p, ws), 0, bits_stage, 1, err_flag));
+  std::vector<double> vals(size_t(p->n_terms));
+  std::vector<double2> host(static_cast<size_t>(tper));
+  // without selectors (every term the identity) one contraction serves all terms
+  const int64_t step = p->n_sel > 0 ? tper : p->n_terms;
+  for (int64_t tb = 0; tb < p->n_terms; tb += step) {
+    const int64_t nt = std::min<int64_t>(tper, p->n_terms - tb);
+    if (!p->traj_leaves.empty()) {
+      TNQ_CUDA(launch_traj_leaves(reinterpret_cast<const TrajLeafDesc*>(ws + p->ws_traj), (int)p->traj_leaves.size(),
+                                  reinterpret_cast<const TrajFactor*>(ws + p->ws_traj_factors),
+                                  reinterpret_cast<const double2*>(ws + p->ws_traj_mats),
+                                  reinterpret_cast<const double*>(ws + p->ws_traj_cumq), ws, 0, uint64_t(tb), t,
+                                  ctx->stream, reinterpret_cast<const int8_t*>(ws + p->ws_picks), p->n_sel,
+                                  p->n_terms));
+      ctx->launches++;
+    }
+    TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
+    for (int s = 0; s < n_slices; ++s) {
+      tnq_status st = run_pass(ctx, p, s, ws, s == 0);
+      if (st != TNQ_OK) return st;
+    }
+    TNQ_CUDA(launch_traj_amplitudes_out(ws + p->ws_acc, 1, 0, nt, nullptr, 0, tpos.data(), t, stage, 1, ctx->stream));
+    ctx->launches++;
+    TNQ_CUDA(cudaMemcpyAsync(host.data(), stage, 16 * size_t(nt), cudaMemcpyDeviceToHost, ctx->stream));
+    TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (p->n_sel > 0) {
+      for (int64_t j = 0; j < nt; ++j) vals[size_t(tb + j)] = host[size_t(j)].x;
+    } else {
+      for (auto& v : vals) v = host[0].x;
+    }
+  }
+  int herr[2] = {0, 0};
+  TNQ_CUDA(cudaMemcpyAsync(herr, err_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->timing) {
+    tnq_status ts = timing_collect(ctx);
+    if (ts != TNQ_OK) return ts;
+  }
+  if (herr[1]) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired; results are invalid");
+  double sum = 0.0;
+  for (int64_t j = 0; j < p->n_terms; ++j) {
+    sum += coeffs[j] * vals[size_t(j)];
+    if (term_values) term_values[j] = vals[size_t(j)];
+  }
+  *value = sum;
+  return TNQ_OK;
 }
 
 // Partial-product bytes any split of an output of 2^rc elements can need.

@@ -52,6 +52,7 @@ tnq_status exec_noisy(Ctx* ctx, Plan* p, int64_t n_traj, uint64_t seed, int64_t 
                       double* p_out, double* se_out);
 tnq_status exec_traj_amplitudes(Ctx* ctx, Plan* p, uint64_t seed, int64_t traj_begin, int64_t n_traj, int64_t n_bs,
                                 const int8_t* bits, double* out);
+tnq_status exec_expectation(Ctx* ctx, Plan* p, const double* coeffs, double* value, double* term_values);
 tnq_status exec_contract_pair(Ctx* ctx, const void* A, int ra, const int* al, const void* B, int rb,
                               const int* bl, void* C, int rc, const int* cl, void* ws, size_t ws_bytes);
 size_t contract_workspace_bytes(int precision, int ra, int rb, int rc);

@@ -16,18 +16,32 @@
 // G is read once from HBM, in its stored bit order (the gather of the permute
 // is fused: the row and K bits of G sit at arbitrary positions of the stored
 // tensor), split into hi/lo parts (BF16 or TF32) by converter warps and written
-// straight into the 128-byte-swizzled K-major layout the MMA reads (one or two
-// 128-byte swizzle atoms per row).  The output is written once.  Per 128-row
+// straight into the 128-byte-swizzled K-major layout the MMA reads (128-byte
+// swizzle atoms of K per row).  The output is written once.  Per 128-row
 // tile: 128 * K * 8 bytes in, 128 * ns * 8 bytes out, 3 * ceil(2K / k_step)
 // MMAs of 128 x Npad (Npad = max(16, 2 ns) <= 256; four TMEM accumulator
 // buffers for Npad <= 64, two above, at most all 512 columns).  When the
 // expanded small operand of every batch entry does not fit in shared memory,
 // each batch entry gets its own launch.
 //
+// A tile's K range may be cut into K-parts of whole atoms: a shared-memory
+// stage then holds one part of a tile (the MMAs of a tile accumulate over its
+// parts), which lets TF32 rows of K = 64 (four atoms per part) run beside a
+// 128 KB expanded small operand.
+//
+// In the split modes the product hi*hi accumulates into one TMEM buffer and
+// the two correction products hi*lo, lo*hi into a second one; the epilogue
+// adds them in FP32 registers.  The tensor-memory accumulator adds each MMA's
+// result with truncation toward zero, so a chain of additions into the large
+// accumulator shrinks it by about half an ulp per addition; keeping the
+// corrections (about 2^-9 of it) apart cuts that chain to one addition per K
+// step.
+//
 // CTA (persistent, one per SM) = 13 warps:
 //   warps 0-7   converters, two groups of four; group g fills the stages of
-//               the CTA's tiles i = g, g + 2, ...: each thread owns one tile
-//               row and walks it in chunks of up to 16 complex values (loads
+//               the CTA's items i = g, g + 2, ... (an item is one K-part of a
+//               tile): each thread owns one tile row and walks the item's K
+//               range in chunks of up to 16 complex values (loads
 //               of 16-byte pairs when the lowest stored bit is a K bit); the
 //               loads of the next chunks are issued before the current one is
 //               split and stored, and the register ring rotates by moves,
@@ -37,8 +51,9 @@
 //   warp 8      allocates TMEM and (one thread) issues the MMAs of each tile
 //               into one of the TMEM accumulator buffers;
 //   warps 9-12  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, 32
-//               columns at a time, and writes complex64 outputs (or adds into
-//               the FP64 cross-slice sum).
+//               columns at a time (and the correction buffer's columns),
+//               and writes complex64 outputs (or adds into the FP64
+//               cross-slice sum).
 // Every mbarrier wait is bounded; one that runs out sets the error flag and
 // the CTA unwinds.
 #include <cuda_bf16.h>
@@ -65,8 +80,8 @@ constexpr int TR_MAX_STAGES = 4;               // even: stage parity = converter
 constexpr int TR_MAX_NACC = 4;                 // TMEM accumulator buffers
 constexpr int TR_ROW_BYTES = 128;              // one swizzle atom of a row
 constexpr int TR_ATOM_BYTES = 128 * TR_ROW_BYTES;  // one atom column of a 128-row tile
-constexpr int TR_STAGE_BUDGET = 128 * 1024;
-constexpr int TR_BPRIME_BUDGET = 64 * 1024;
+constexpr int TR_BPRIME_BUDGET = 128 * 1024;
+constexpr int TR_SMEM_LIMIT = 225 * 1024;      // dynamic shared memory of one CTA
 constexpr int TR_KMAX = 64;
 
 struct TrParams {
@@ -75,11 +90,17 @@ struct TrParams {
   GatherDesc gd;          // rows: g bits then batch bits; K bits in contraction order
   int ns, ng, K, batch;
   int npad;               // MMA N: max(16, 2 ns)
-  int nks;                // MMA K steps (32 bytes of K per step)
-  int atoms;              // 128-byte swizzle atoms per row (1 or 2)
-  int stages;             // shared-memory stages (4 with one atom, 2 with two)
+  int nks;                // MMA K steps (32 bytes of K per step) of a whole row
+  int atoms;              // 128-byte swizzle atoms per row (1 to 4)
+  int kparts;             // K-parts per tile (items per tile)
+  int patoms;             // atoms per part: atoms / kparts
+  int nks_part;           // MMA K steps per part
+  int kc;                 // complex values per part
+  int stages;             // shared-memory stages, each holding one part (even)
   int nacc;               // TMEM accumulator buffers
-  int nchunks;            // converter chunks per row
+  int dual;               // 1: correction products in a second TMEM buffer
+  int acc_cols;           // TMEM columns per accumulator buffer: npad, or 2 npad when dual
+  int nchunks;            // converter chunks per part
   int kind_bf16;          // 1: BF16 parts, kind::f16; 0: TF32 parts, kind::tf32
   int split;              // 1: three products (hi/lo); 0: one TF32 product
   int pairs;              // the lowest stored bit of G is K bit 0: 16-byte loads
@@ -203,11 +224,11 @@ __device__ __forceinline__ size_t deposit(long long v, const int* pos, int n) {
   return o;
 }
 
-// Chunk c of the row whose K = 0 element sits at stored offset `base`.
+// Chunk c of K-part kp of the row whose K = 0 element sits at stored offset `base`.
 template <int CH>
-__device__ __forceinline__ void load_chunk(const TrParams& P, const uint32_t* koff, size_t base, int c,
+__device__ __forceinline__ void load_chunk(const TrParams& P, const uint32_t* koff, size_t base, int kp, int c,
                                            float2 (&v)[CH]) {
-  const int k0 = c * CH;
+  const int k0 = kp * P.kc + c * CH;
   if (P.pairs) {
 #pragma unroll
     for (int j = 0; j < CH; j += 2) {
@@ -234,12 +255,12 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
   __shared__ uint32_t koff[TR_KMAX];
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t stage_bytes = 2u * TR_ATOM_BYTES * uint32_t(P.atoms);  // hi + lo
+  const uint32_t stage_bytes = 2u * TR_ATOM_BYTES * uint32_t(P.patoms);  // hi + lo of one K-part
   uint8_t* bprime = smem + size_t(P.stages) * stage_bytes;
   const uint32_t bp_atom = uint32_t(P.npad) * TR_ROW_BYTES;
   const uint32_t bp_half = bp_atom * uint32_t(P.atoms);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t tmem_cols = uint32_t(P.npad * P.nacc) < 32u ? 32u : uint32_t(P.npad * P.nacc);
+  const uint32_t tmem_cols = uint32_t(P.acc_cols * P.nacc) < 32u ? 32u : uint32_t(P.acc_cols * P.nacc);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) {
@@ -272,46 +293,54 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  const uint32_t tph = uint32_t(P.tiles_per_h), total = uint32_t(P.total_tiles);
+  const int kparts = P.kparts;
 
   if (warp < TR_CONV_WARPS) {
-    // ---------------- converters: group grp fills the stages of tiles grp, grp+2, ...
+    // ---------------- converters: group grp fills the stages of items grp, grp+2, ...
+    // CTA-local item j is K-part j % kparts of the CTA's tile j / kparts
+    // (global tile blockIdx.x + (j / kparts) * gridDim.x); it uses stage
+    // j % stages, phase (j / stages) & 1.
     const int grp = warp >> 2, r = (warp & 3) * 32 + lane;
     const int nhi = P.gd.nrow - 7;
-    const int nch = P.nchunks, units = 2 * P.nks;
+    const int nch = P.nchunks, units = 2 * P.nks_part;
     size_t soff = 0;
     for (int j = 0; j < P.gd.n_slice; ++j)
       if (P.gd.slice_src[j] >= 0 && ((P.slice_id >> j) & 1)) soff |= size_t(1) << P.gd.slice_src[j];
     const size_t lo = soff | deposit(r, P.gd.rowpos, 7);
-    const uint32_t tph = uint32_t(P.tiles_per_h), total = uint32_t(P.total_tiles), stride2 = 2u * gridDim.x;
     auto row_base = [&](uint32_t t) {
       const uint32_t h = t / tph, g0 = (t - h * tph) * 128u;
       return lo | deposit(((long long)h * P.ng + g0) >> 7, P.gd.rowpos + 7, nhi);
     };
-    // items (tile, chunk c) in order: the loads of the next DEPTH items are in
-    // flight while one is split and stored.  Tile i of this CTA (global tile
-    // blockIdx.x + i * gridDim.x) uses stage i % stages, phase (i / stages) & 1.
-    const uint32_t t0 = blockIdx.x + uint32_t(grp) * gridDim.x;
-    uint32_t tl = t0;  // load cursor
+    auto item_tile = [&](uint32_t j) { return blockIdx.x + (j / uint32_t(kparts)) * gridDim.x; };
+    // items (item, chunk c) in order: the loads of the next DEPTH chunks are in
+    // flight while one is split and stored.
+    uint32_t jl = uint32_t(grp);  // load cursor: item, chunk, its tile's row base
+    uint32_t tl = item_tile(jl);
     int cl = 0;
     size_t bl = tl < total ? row_base(tl) : 0;
     auto advance_load = [&]() {
       if (++cl == nch) {
         cl = 0;
-        tl += stride2;
-        bl = tl < total ? row_base(tl) : 0;
+        jl += 2;
+        const uint32_t tn = item_tile(jl);
+        if (tn != tl) {
+          tl = tn;
+          bl = tl < total ? row_base(tl) : 0;
+        }
       }
     };
     float2 buf[DEPTH + 1][CH];
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d) {
-      if (tl < total) load_chunk<CH>(P, koff, bl, cl, buf[d]);
+      if (tl < total) load_chunk<CH>(P, koff, bl, int(jl % uint32_t(kparts)), cl, buf[d]);
       advance_load();
     }
-    uint32_t t = t0;  // convert cursor
+    uint32_t jc = uint32_t(grp);  // convert cursor
     int s = grp, c = 0;
     uint32_t ph = 0;
-    while (t < total) {
-      if (tl < total) load_chunk<CH>(P, koff, bl, cl, buf[DEPTH]);
+    while (item_tile(jc) < total) {
+      if (tl < total) load_chunk<CH>(P, koff, bl, int(jl % uint32_t(kparts)), cl, buf[DEPTH]);
       advance_load();
       if (c == 0 && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
         atomicOr(P.err, 1);
@@ -322,7 +351,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       if (c == nch - 1) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&full_bar[s]));
-        s += 2;  // this group's next tile
+        s += 2;  // this group's next item
         if (s >= P.stages) {
           s -= P.stages;
           ph ^= 1;
@@ -334,47 +363,54 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
         for (int j = 0; j < CH; ++j) buf[d][j] = buf[d + 1][j];
       if (++c == nch) {
         c = 0;
-        t += stride2;
+        jc += 2;
       }
     }
   } else if (warp == TR_MMA_WARP) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      const uint32_t tph = uint32_t(P.tiles_per_h), total = uint32_t(P.total_tiles);
       int s = 0, b = 0;
       uint32_t sph = 0, bph = 0;  // phases of the stage ring and of the accumulator ring
       bool drained = false;       // every accumulator buffer has been used once
-      for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+      bool ok = true;
+      for (uint32_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
         if (drained && !mbar_wait(smem_u32(&acc_empty[b]), bph ^ 1)) {
           atomicOr(P.err, 1);
           break;
         }
-        if (!mbar_wait(smem_u32(&full_bar[s]), sph)) {
-          atomicOr(P.err, 1);
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t h = t / tph;
-        const uint32_t a_hi = smem_u32(smem + size_t(s) * stage_bytes), a_lo = a_hi + stage_bytes / 2;
         const uint32_t b_hi = smem_u32(bprime) + h * 2 * bp_half, b_lo = b_hi + bp_half;
-        const uint32_t d = tmem + uint32_t(b * P.npad);
-        for (int kk = 0; kk < P.nks; ++kk) {
-          const uint32_t ao = uint32_t(kk >> 2) * TR_ATOM_BYTES + uint32_t(kk & 3) * 32;
-          const uint32_t bo = uint32_t(kk >> 2) * bp_atom + uint32_t(kk & 3) * 32;
-          if (P.split) {
-            mma_issue(P.kind_bf16, d, smem_desc(a_lo + ao), smem_desc(b_hi + bo), P.idesc, kk > 0 ? 1u : 0u);
-            mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_lo + bo), P.idesc, 1u);
-            mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, 1u);
-          } else {
-            mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, kk > 0 ? 1u : 0u);
+        const uint32_t d = tmem + uint32_t(b * P.acc_cols);
+        const uint32_t dc = P.dual ? d + uint32_t(P.npad) : d;  // correction products
+        for (int kp = 0; kp < kparts; ++kp) {
+          if (!mbar_wait(smem_u32(&full_bar[s]), sph)) {
+            atomicOr(P.err, 1);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_hi = smem_u32(smem + size_t(s) * stage_bytes), a_lo = a_hi + stage_bytes / 2;
+          for (int kk = 0; kk < P.nks_part; ++kk) {
+            const int kg = kp * P.nks_part + kk;  // K step within the row
+            const uint32_t ao = uint32_t(kk >> 2) * TR_ATOM_BYTES + uint32_t(kk & 3) * 32;
+            const uint32_t bo = uint32_t(kg >> 2) * bp_atom + uint32_t(kg & 3) * 32;
+            const uint32_t acc_on = kg > 0 ? 1u : 0u;
+            if (P.split) {
+              mma_issue(P.kind_bf16, dc, smem_desc(a_lo + ao), smem_desc(b_hi + bo), P.idesc, acc_on);
+              mma_issue(P.kind_bf16, dc, smem_desc(a_hi + ao), smem_desc(b_lo + bo), P.idesc, 1u);
+              mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, P.dual ? acc_on : 1u);
+            } else {
+              mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, acc_on);
+            }
+          }
+          mma_commit(smem_u32(&empty_bar[s]));
+          if (++s == P.stages) {
+            s = 0;
+            sph ^= 1;
           }
         }
-        mma_commit(smem_u32(&empty_bar[s]));
+        if (!ok) break;
         mma_commit(smem_u32(&acc_full[b]));
-        if (++s == P.stages) {
-          s = 0;
-          sph ^= 1;
-        }
         if (++b == P.nacc) {
           b = 0;
           bph ^= 1;
@@ -389,7 +425,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
     const int quarter = warp & 3;
     const uint32_t lane_addr = uint32_t(quarter * 32) << 16;
     const int row = quarter * 32 + lane;
-    const uint32_t tph = uint32_t(P.tiles_per_h), total = uint32_t(P.total_tiles);
     int b = 0;
     uint32_t bph = 0;
     for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
@@ -402,13 +437,22 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       const uint32_t h = t / tph;
       const uint32_t g = (t - h * tph) * 128u + uint32_t(row);
       const size_t obase = size_t(h) * P.ns * P.ng + size_t(g) * P.g_stride;
-      const uint32_t base = tmem + lane_addr + uint32_t(b * P.npad);
+      const uint32_t base = tmem + lane_addr + uint32_t(b * P.acc_cols);
       // 32 columns (16 outputs) at a time
       for (int c0 = 0; c0 < P.npad; c0 += 32) {
         uint32_t v[32];
         TC_LD16(base + c0, v);
         if (c0 + 16 < P.npad) TC_LD16(base + c0 + 16, (v + 16));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (P.dual) {
+          uint32_t w[32];
+          TC_LD16(base + P.npad + c0, w);
+          if (c0 + 16 < P.npad) TC_LD16(base + P.npad + c0 + 16, (w + 16));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+        } else {
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int s = c0 / 2 + j;
@@ -459,7 +503,32 @@ size_t tr_bprime_bytes(int ns, int K, int batch, bool bf16) {
   return size_t(batch) * 2 * tr_atoms(K, bf16) * tr_npad(ns) * TR_ROW_BYTES;
 }
 
-constexpr size_t TR_SMEM_MAX = size_t(TR_STAGE_BUDGET) + TR_BPRIME_BUDGET + 1024;
+// Stage layout of a launch: K-parts per tile and stages.  A row of one or two
+// atoms is one part (four stages with one atom, two with two); longer rows
+// (TF32 with K = 64: four atoms) are cut into one-atom parts.  The stages plus
+// the expanded small operand (bprime bytes) must fit the shared-memory limit.
+struct TrStages {
+  int kparts = 0, patoms = 0, stages = 0;
+};
+
+TrStages tr_stages(int atoms, size_t bprime) {
+  TrStages t;
+  if (atoms <= 2) {
+    t.kparts = 1;
+    t.patoms = atoms;
+    t.stages = atoms == 1 ? 4 : 2;
+  } else {
+    t.kparts = atoms;
+    t.patoms = 1;
+    t.stages = 4;
+  }
+  const size_t stage_bytes = size_t(2) * TR_ATOM_BYTES * t.patoms;
+  while (t.stages > 2 && size_t(t.stages) * stage_bytes + bprime + 1024 > size_t(TR_SMEM_LIMIT)) t.stages -= 2;
+  if (size_t(t.stages) * stage_bytes + bprime + 1024 > size_t(TR_SMEM_LIMIT)) t.stages = 0;
+  return t;
+}
+
+constexpr size_t TR_SMEM_MAX = size_t(TR_SMEM_LIMIT);
 
 }  // namespace
 
@@ -478,11 +547,12 @@ cudaError_t tc_rows_prepare() {
 bool tc_rows_supported(int ns, int ng, int K, int batch, int nrow, int precision) {
   if (precision != TNQ_PREC_TF32 && precision != TNQ_PREC_TF32X3 && precision != TNQ_PREC_BF16X3) return false;
   const bool bf16 = precision == TNQ_PREC_BF16X3;
-  // rows of 2K reals span at most two swizzle atoms; MMA N = 2 ns <= 256
-  if (ns < 1 || ns > 128 || K < 1 || K > (bf16 ? 64 : 32) || ng < 128 || (ng & 127) || batch < 1 || nrow < 7)
-    return false;
-  // S' of one batch entry must fit (larger batches run one launch per entry)
-  return tr_bprime_bytes(ns, K, 1, bf16) <= size_t(TR_BPRIME_BUDGET);
+  // rows of 2K reals span at most four swizzle atoms; MMA N = 2 ns <= 256
+  if (ns < 1 || ns > 128 || K < 1 || K > TR_KMAX || ng < 128 || (ng & 127) || batch < 1 || nrow < 7) return false;
+  // S' of one batch entry must fit beside at least two stages (larger batches
+  // run one launch per entry)
+  const size_t bp = tr_bprime_bytes(ns, K, 1, bf16);
+  return bp <= size_t(TR_BPRIME_BUDGET) && tr_stages(tr_atoms(K, bf16), bp).stages >= 2;
 }
 
 namespace {
@@ -504,10 +574,18 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   const int k_step = P.kind_bf16 ? 8 : 4;  // complex values per 32-byte MMA K step
   P.nks = (K + k_step - 1) / k_step;
   P.atoms = tr_atoms(K, P.kind_bf16 != 0);
-  P.stages = P.atoms == 1 ? 4 : 2;
-  P.nacc = P.npad <= 64 ? 4 : 2;  // TMEM: npad * nacc <= 512 columns
-  const int ch = K <= 8 ? 8 : 16;
-  P.nchunks = (K + ch - 1) / ch;
+  const TrStages ts = tr_stages(P.atoms, tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0));
+  if (ts.stages < 2) return cudaErrorNotSupported;
+  P.kparts = ts.kparts;
+  P.patoms = ts.patoms;
+  P.stages = ts.stages;
+  P.nks_part = P.kparts == 1 ? P.nks : 4 * P.patoms;  // parts of several atoms hold whole atoms of K
+  P.kc = P.kparts == 1 ? K : P.patoms * TR_ROW_BYTES / (2 * (P.kind_bf16 ? 2 : 4));
+  P.nacc = P.npad <= 64 ? 4 : 2;  // TMEM: acc_cols * nacc <= 512 columns
+  P.dual = (P.split && P.npad <= 128) ? 1 : 0;
+  P.acc_cols = P.npad * (P.dual ? 2 : 1);
+  const int ch = P.kc <= 8 ? 8 : 16;
+  P.nchunks = (P.kc + ch - 1) / ch;
   P.pairs = gd.nk >= 1 && gd.kpos[0] == 0;
   P.s_stride = s_stride_out;
   P.g_stride = g_stride_out;
@@ -522,8 +600,8 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   P.acc = reinterpret_cast<double2*>(acc);
   P.err = err;
   const long long grid = std::min<long long>(P.total_tiles, std::max(1, sm_count));
-  const size_t smem = size_t(P.stages) * 2 * P.atoms * TR_ATOM_BYTES + tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0) +
-                      1024;
+  const size_t smem = size_t(P.stages) * 2 * P.patoms * TR_ATOM_BYTES +
+                      tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0) + 1024;
   if (ch == 8)
     cgemm_tc_rows_kernel<8, 4><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   else
@@ -541,7 +619,8 @@ cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const Gat
   cudaError_t pe = tc_rows_prepare();
   if (pe != cudaSuccess) return pe;
   const bool bf16 = precision == TNQ_PREC_BF16X3;
-  if (tr_bprime_bytes(ns, K, batch, bf16) <= size_t(TR_BPRIME_BUDGET))
+  const size_t bp_all = tr_bprime_bytes(ns, K, batch, bf16);
+  if (bp_all <= size_t(TR_BPRIME_BUDGET) && tr_stages(tr_atoms(K, bf16), bp_all).stages >= 2)
     return launch_tc_rows_one(Ssmall, Gsrc, gd, C, acc, ns, ng, K, batch, s_stride_out, g_stride_out, slice_id,
                               precision, err, sm_count, st);
   // S' of every batch entry does not fit: one launch per entry, whose batch

@@ -32,12 +32,17 @@ struct COp {
   std::vector<std::vector<cd>> mats;    // gate: 1 matrix; channel: Kraus operators
   std::vector<double> kraus_q;          // channel: q_k = Tr(A_k^dag A_k)/d
   int channel_index = -1;               // channel: running index in circuit order
+  // selector (channel == true): one of mats is applied per term, chosen by a
+  // pick table (the Pauli operators of an observable), without rescaling
+  bool selector = false;
+  int selector_index = -1;
 };
 
 struct Circuit {
   int n = 0;
   std::vector<COp> ops;
   int n_channels = 0;
+  int n_selectors = 0;
 };
 
 // ---------------------------------------------------------------- network
@@ -151,6 +156,14 @@ struct Plan {
   // doubled density-matrix network (Sec. 3.3): results are the real numbers
   // <<x, x|rho>> = p(x), written as one double per bitstring
   bool density = false;
+  // expectation values (Sec. 3.1.2): conjugate network with Pauli selectors;
+  // picks[t * n_sel + j] = Pauli (0 I, 1 X, 2 Y, 3 Z) of term t on selector j
+  bool expectation = false;
+  int64_t n_terms = 0;
+  int n_sel = 0;
+  int kept_gates = 0;             // gates of the circuit inside the observable's light cone
+  std::vector<int8_t> picks;
+  size_t ws_picks = 0;
   // workspace layout (bytes)
   // persist: outputs of slice-invariant steps read by slice-dependent steps
   // (kept for the whole batch, outside the reusable arena)

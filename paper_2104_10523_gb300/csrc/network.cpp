@@ -104,7 +104,7 @@ tnq_status build_network(const Circuit& c, int batch_log2, int traj_log2, const 
   net.row_len = row_len > 0 ? row_len : c.n;
   const int n = c.n;
   const int nops = (int)c.ops.size();
-  net.noisy = c.n_channels > 0;
+  net.noisy = c.n_channels > 0 || c.n_selectors > 0;
 
   // --- group assignment
   std::vector<int> group_of(nops, -1);

@@ -236,10 +236,11 @@ void layout_steps(Plan* p) {
   const size_t n_open = p->net.open_qubits.size();
   p->ws_bits = off + 256;
   p->ws_out_stage = align_up(p->ws_bits + size_t(p->net.row_len) * per, 256);
-  p->ws_psum = align_up(p->ws_out_stage + ((16 * per) << n_open), 256);
+  p->ws_psum = align_up(p->ws_out_stage + std::max((16 * per) << n_open, size_t(16) << p->traj_log2), 256);
   p->ws_p2sum = align_up(p->ws_psum + 8 * per, 256);
   p->ws_qtab = align_up(p->ws_p2sum + 8 * per, 256);
-  off = align_up(p->ws_qtab + 4 * (p->net.proj_src.size() + n_open), 256);
+  p->ws_picks = align_up(p->ws_qtab + 4 * (p->net.proj_src.size() + n_open), 256);
+  off = align_up(p->ws_picks + p->picks.size(), 256);
   p->ws_total = off;
 }
 
@@ -282,6 +283,14 @@ static void build_traj_program(const Circuit& c, Plan* p) {
       f.chan_index = op.channel_index;
       if (!op.channel) {
         f.mat_off = push_mat(op.mats[0]);
+      } else if (op.selector) {
+        f.channel = 2;
+        f.n_ops = (int)op.mats.size();
+        f.chan_index = op.selector_index;
+        for (int k = 0; k < f.n_ops; ++k) {
+          int idx = push_mat(op.mats[k]);
+          if (k == 0) f.mat_off = idx;
+        }
       } else {
         f.n_ops = (int)op.mats.size();
         f.cum_off = (int)p->traj_cumq.size();
@@ -352,7 +361,7 @@ tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, c
   if (o.max_intermediate_log2 < 1 || o.max_intermediate_log2 > 31)
     return fail(TNQ_ERR_INVALID_ARG, "max_intermediate_log2 must be in [1, 31]");
   p->batch_log2 = o.batch_log2;
-  p->traj_log2 = c.n_channels > 0 ? o.traj_log2 : 0;
+  p->traj_log2 = (c.n_channels > 0 || c.n_selectors > 0) ? o.traj_log2 : 0;
   tnq_status st = build_network(c, p->batch_log2, p->traj_log2, spec.open, spec.row_len, &p->net);
   if (st != TNQ_OK) return st;
   p->hyper = make_hyper(p->net);

@@ -27,7 +27,7 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __global__ void traj_leaf_kernel(const TrajLeafDesc* __restrict__ leaves, int n_leaves,
                                  const TrajFactor* __restrict__ factors, const double2* __restrict__ mats,
                                  const double* __restrict__ cumq, char* ws, uint64_t seed, uint64_t traj_base,
-                                 int traj_log2) {
+                                 int traj_log2, const int8_t* __restrict__ picks, int n_sel, int64_t n_terms) {
   const long long T = 1ll << traj_log2;
   const long long total = (long long)n_leaves * T;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -42,7 +42,10 @@ __global__ void traj_leaf_kernel(const TrajLeafDesc* __restrict__ leaves, int n_
     for (int f = 0; f < L.n_factors; ++f) {
       const TrajFactor F = factors[L.factor_off + f];
       int mi = F.mat_off;
-      if (F.channel) {
+      if (F.channel == 2) {
+        const int64_t term = int64_t(traj_base) + tau;
+        mi += term < n_terms ? int(picks[term * n_sel + F.chan_index]) : 0;
+      } else if (F.channel) {
         const double u = draw_uniform(seed, traj_base + uint64_t(tau), uint64_t(F.chan_index));
         int k = F.n_ops - 1;
         for (int j = 0; j < F.n_ops; ++j)
@@ -162,11 +165,12 @@ unsigned blocks_for(int64_t n) { return unsigned(std::max<int64_t>(1, std::min<i
 
 cudaError_t launch_traj_leaves(const TrajLeafDesc* leaves, int n_leaves, const TrajFactor* factors,
                                const double2* mats, const double* cumq, char* ws, uint64_t seed,
-                               uint64_t traj_base, int traj_log2, cudaStream_t st) {
+                               uint64_t traj_base, int traj_log2, cudaStream_t st, const int8_t* picks, int n_sel,
+                               int64_t n_terms) {
   if (n_leaves == 0) return cudaSuccess;
   const int64_t total = int64_t(n_leaves) << traj_log2;
   traj_leaf_kernel<<<blocks_for(total), 256, 0, st>>>(leaves, n_leaves, factors, mats, cumq, ws, seed, traj_base,
-                                                      traj_log2);
+                                                      traj_log2, picks, n_sel, n_terms);
   return cudaGetLastError();
 }
 

@@ -15,14 +15,16 @@ namespace tnq {
 
 // One factor of a trajectory leaf's operator, in circuit order.
 struct TrajFactor {
-  int channel;     // 0: fixed gate matrix at mat_off; 1: Kraus channel
+  int channel;     // 0: fixed gate matrix at mat_off; 1: Kraus channel; 2: operator
+                   // selected per term from a pick table (Pauli observables)
   int arity;       // 1 or 2 (qubits the op acts on)
   int slot_mask;   // group slots the op acts on: 1, 2 or 3
   int swap;        // two-qubit op listed as (slot 1, slot 0)
   int mat_off;     // gate: index of its matrix; channel: index of A_0 / sqrt(q_0)
   int n_ops;       // channel: number of Kraus operators
   int cum_off;     // channel: index of q_0 in the cumulative-probability table
-  int chan_index;  // channel: running channel index c in circuit order
+  int chan_index;  // channel: running channel index c in circuit order; selector: its column
+                   // in the pick table
 };
 
 struct TrajLeafDesc {
@@ -37,9 +39,13 @@ struct TrajLeafDesc {
 // Builds every trajectory leaf for trajectories [traj_base, traj_base + 2^traj_log2).
 // mats: complex128 matrices (row-major, 2x2 or 4x4) at the offsets the
 // factors name (each matrix takes 16 entries); cumq: cumulative probabilities.
+// Selector factors of trajectory (term) t use matrix mat_off + picks[t * n_sel
+// + chan_index] (picks: device int8 [n_terms][n_sel]; terms t >= n_terms, the
+// padding of a last pass, take pick 0).
 cudaError_t launch_traj_leaves(const TrajLeafDesc* leaves, int n_leaves, const TrajFactor* factors,
                                const double2* mats, const double* cumq, char* ws, uint64_t seed,
-                               uint64_t traj_base, int traj_log2, cudaStream_t st);
+                               uint64_t traj_base, int traj_log2, cudaStream_t st, const int8_t* picks = nullptr,
+                               int n_sel = 0, int64_t n_terms = 0);
 
 // For b < nb: psum[b] += sum_{t < nt} |amp(b, t)|^2, p2sum[b] += sum_t |amp|^4, with
 // amp(b, t) = acc[pdep(b, bpos) | pdep(t, tpos)] (FP64, trajectories in order).

@@ -42,7 +42,7 @@ EXPORTS = (
     "tnq_cost_model_gradients", "tnq_cost_model_train", "tnq_cost_model_predict", "tnq_plan_step_features",
     "tnq_plan_create_learned", "tnq_plan_get_candidates", "tnq_plan_autotune", "tnq_amplitudes_slices",
     "tnq_plan_get_tree", "tnq_plan_get_leaf_wires", "tnq_ctx_set_kernel_policy", "tnq_plan_create_open",
-    "tnq_plan_create_density", "tnq_density_probabilities",
+    "tnq_plan_create_density", "tnq_density_probabilities", "tnq_plan_create_expectation", "tnq_expectation",
 )
 
 
@@ -135,6 +135,8 @@ def load() -> C.CDLL:
         "tnq_plan_create_open": ([vp, C.POINTER(TnqPlanOpts), i32, ip, C.POINTER(vp)], i32),
         "tnq_plan_create_density": ([vp, C.POINTER(TnqPlanOpts), C.POINTER(vp)], i32),
         "tnq_density_probabilities": ([vp, vp, i64, vp, vp], i32),
+        "tnq_plan_create_expectation": ([vp, C.POINTER(TnqPlanOpts), i64, C.c_char_p, C.POINTER(vp)], i32),
+        "tnq_expectation": ([vp, vp, dp, dp, dp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -216,6 +218,31 @@ def tnq_plan_create_density(circ_h, max_intermediate_log2=28, batch_log2=0, path
 def tnq_density_probabilities(ctx, plan, bits, p_out):
     """bits: int8 [n_bs][n] (host or device); p_out: float64 [n_bs] (same choices)."""
     check(load().tnq_density_probabilities(ctx, plan, int(bits.shape[0]), _ptr(bits), _ptr(p_out)))
+
+
+def tnq_plan_create_expectation(circ_h, paulis, max_intermediate_log2=28, traj_log2=6, path_mode=TNQ_PATH_BEST,
+                                n_candidates=16, seed=0):
+    """paulis: list of strings over "IXYZ", one per term, each of length n_qubits."""
+    n = load().tnq_circuit_n_qubits(circ_h)
+    if any(len(ps) != n for ps in paulis):
+        raise ValueError("every Pauli string must have one character per qubit")
+    o = TnqPlanOpts(max_intermediate_log2, 0, traj_log2, path_mode, n_candidates, seed)
+    h = C.c_void_p()
+    check(load().tnq_plan_create_expectation(circ_h, C.byref(o), len(paulis), "".join(paulis).encode(), C.byref(h)))
+    return h
+
+
+def tnq_expectation(ctx, plan, coeffs):
+    """(value, per-term values) for real coefficients [n_terms]."""
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    v = C.c_double()
+    tv = np.zeros(c.shape[0])
+    check(load().tnq_expectation(ctx, plan, c.ctypes.data_as(dp_t()), C.byref(v), tv.ctypes.data_as(dp_t())))
+    return float(v.value), tv
+
+
+def dp_t():
+    return C.POINTER(C.c_double)
 
 
 def tnq_plan_destroy(h):
@@ -450,9 +477,11 @@ class Circuit:
 class Plan:
     """Owns a tnq_plan; info() and steps() describe it."""
 
-    def __init__(self, circuit: Circuit, open_qubits=None, density=False, **opts):
+    def __init__(self, circuit: Circuit, open_qubits=None, density=False, paulis=None, **opts):
         self.circuit = circuit
-        if density:
+        if paulis is not None:
+            self.h = tnq_plan_create_expectation(circuit.h, list(paulis), **opts)
+        elif density:
             self.h = tnq_plan_create_density(circuit.h, **opts)
         elif open_qubits:
             self.h = tnq_plan_create_open(circuit.h, list(open_qubits), **opts)
@@ -532,6 +561,10 @@ class Context:
         p = np.empty(b.shape[0], dtype=np.float64)
         tnq_density_probabilities(self.h, plan.h, b, p)
         return p
+
+    def expectation(self, plan: Plan, coeffs):
+        """(<psi|H|psi>, per-term <psi|P_t|psi>) for an expectation-value plan."""
+        return tnq_expectation(self.h, plan.h, coeffs)
 
     def noisy_probabilities(self, plan: Plan, bits, n_traj, seed):
         """(p, stderr) as float64 arrays for host int8 bits [n_bs][n]."""

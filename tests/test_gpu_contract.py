@@ -139,3 +139,48 @@ def test_invalid_labels_rejected(T):
     with pytest.raises(T.TnqError) as e:
         T.tnq_contract_pair(ctx.h, A, [0, 1], A, [1, 2], A, [0, 5], ws, 1 << 16)
     assert e.value.status == T.TNQ_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("shape", [(6, 16, 6), (5, 16, 6), (6, 15, 5), (4, 17, 6), (6, 14, 3)])
+def test_tall_skinny_long_k(T, prec, shape):
+    """Tall-skinny steps of the benchmark's shape class (2^s <= 64 small rows,
+    2^g large rows, K = 2^k up to 64, operand bits scattered) run on the
+    tall-skinny tcgen05 kernel (timing kind 5) in every tensor-core mode; in
+    TF32 with K = 64 a 128-row tile passes through shared memory in four
+    K-parts.  The split modes keep the correction products in their own TMEM
+    accumulator, so TF32x3 stays within a few FP32 roundings of the FP64
+    result."""
+    import torch
+    ns, ng, nk = shape
+    rng = np.random.default_rng(100 + ns + ng + nk)
+    small, big, kl = list(range(40, 40 + ns)), list(range(60, 60 + ng)), list(range(nk))
+    al = list(rng.permutation(small + kl))
+    bl = list(rng.permutation(big + kl))
+    ol = list(rng.permutation(small + big))
+    A = ((rng.standard_normal(2 ** len(al)) + 1j * rng.standard_normal(2 ** len(al))) / 2 ** (nk / 2)).astype(np.complex64)
+    B = (rng.standard_normal(2 ** len(bl)) + 1j * rng.standard_normal(2 ** len(bl))).astype(np.complex64)
+    ctx = T.Context(0, prec)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Ct = torch.full((2 ** len(ol),), float("nan"), dtype=torch.complex64, device="cuda")
+    nb = T.tnq_contract_workspace_bytes(T.PRECISIONS[prec], len(al), len(bl), len(ol))
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    T.tnq_ctx_set_timing(ctx.h, True)
+    T.tnq_contract_pair(ctx.h, At, al, Bt, bl, Ct, ol, ws, nb)
+    kinds = T.tnq_ctx_get_timings(ctx.h)[:, 0].astype(int)
+    assert 5 in kinds, kinds
+    C = Ct.cpu().numpy()
+    rows = rng.choice(2 ** ns, size=min(8, 2 ** ns), replace=False)
+    # sampled output rows of the small operand's index, exact in FP64
+    ref = contraction.sampled_rows(A, al, B, bl, ol, rows, small)
+    lab_rest = [l for l in ol if l not in small]
+    got = np.empty_like(ref)
+    for i, r in enumerate(rows):
+        fix = {l: (int(r) >> j) & 1 for j, l in enumerate(small)}
+        sub = C.reshape((2,) * len(ol))[tuple(fix[l] if l in fix else slice(None) for l in reversed(ol))]
+        axes = [l for l in reversed(ol) if l not in fix]
+        got[i] = np.transpose(sub, [axes.index(l) for l in reversed(lab_rest)]).reshape(-1)
+    err = rel(got, ref)
+    bound = {"tf32x3": 2e-6, "bf16x3": 2e-5, "tf32": 5e-3}[prec]
+    print(f"tall-skinny {shape} {prec}: rel L2 vs FP64 {err:.2e}")
+    assert err <= bound, (prec, shape, err)

@@ -201,3 +201,19 @@ def test_open_plan_validation():
     with pytest.raises(tnq.TnqError) as e:
         tnq.Plan(noisy, open_qubits=[0])
     assert e.value.status == tnq.TNQ_ERR_NOT_SUPPORTED
+
+
+def test_expectation_plan_validation():
+    c = tnq.Circuit(grid_circuit(2, 2, 2, 1))
+    with pytest.raises(tnq.TnqError) as e:
+        tnq.Plan(c, paulis=["XQII"])
+    assert e.value.status == tnq.TNQ_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        tnq.Plan(c, paulis=["XI"])
+    p = tnq.Plan(c, paulis=["ZIII", "IXII", "IIYZ"], traj_log2=6)
+    # the terms share one contraction per pass: 2 term bits are enough for 3 terms
+    assert p.info["traj_log2"] == 2
+    noisy = tnq.Circuit(noisy_grid_circuit(2, 2, 2, 1, 1e-3, 1e-3))
+    with pytest.raises(tnq.TnqError) as e:
+        tnq.Plan(noisy, paulis=["ZIII"])
+    assert e.value.status == tnq.TNQ_ERR_NOT_SUPPORTED
