@@ -442,6 +442,28 @@ def test_trajectory_estimator_exactly_unbiased():
     assert np.allclose(acc, exact, atol=1e-14)
 
 
+def test_trajectory_standard_error_closed_form():
+    """X then one amplitude-damping channel on one qubit: a trajectory picks
+    A_0 (probability 1 - gamma/2) and gives |amp(1)|^2 = v = (1-gamma)/(1-gamma/2),
+    or A_1 and gives 0.  With j jumps among n trajectories (counted from the
+    pinned counter-based uniforms: a jump is u >= 1 - gamma/2) the estimate is
+    m = (n-j) v / n and the standard error sqrt((m v - m^2) / (n - 1)), since
+    the mean of |amp|^4 is (n-j) v^2 / n.  For bitstring 0 the values are 0 or
+    2: m0 = 2 j / n."""
+    gamma, n, seed = 0.3, 200, 12345
+    c = Circuit(1).gate(X, 0).channel(amplitude_damping(gamma), 0)
+    j = sum(1 for t in range(n) if noise.uniform(seed, t, 0) >= 1 - gamma / 2)
+    assert 10 < j < 60   # the sample holds both outcomes
+    v = (1 - gamma) / (1 - gamma / 2)
+    m1 = (n - j) * v / n
+    se1 = np.sqrt((m1 * v - m1 * m1) / (n - 1))
+    m0 = 2.0 * j / n
+    se0 = np.sqrt((m0 * 2.0 - m0 * m0) / (n - 1))
+    mean, se = noise.noisy_probabilities(c, [[1], [0]], n, seed, sv.amplitudes)
+    assert abs(mean[0] - m1) < 1e-14 and abs(se[0] - se1) < 1e-14
+    assert abs(mean[1] - m0) < 1e-14 and abs(se[1] - se0) < 1e-14
+
+
 def test_trajectory_mean_within_stderr_of_density_matrix():
     c = noisy_grid_circuit(2, 2, 4, seed=3, p_depol=0.05, gamma=0.05)
     bits = random_bitstrings(4, 6, 1)
