@@ -106,6 +106,8 @@ typedef struct {
   double search_ms;          /* host time of the path search and slicing */
   size_t workspace_bytes;    /* device bytes tnq_plan_bind needs */
   int n_open;                /* open qubits (tnq_plan_create_open); 0 otherwise */
+  int64_t distinct_trajectories; /* distinct Kraus pick sequences the last
+                                    tnq_noisy_probabilities call contracted */
 } tnq_plan_info;
 
 /* ---- library ---------------------------------------------------------- */
@@ -263,7 +265,11 @@ tnq_status tnq_expectation(tnq_ctx* ctx, tnq_plan* p, const double* coeffs, doub
  * trajectories (Eq. kraus_sum channels, one Kraus operator drawn per channel
  * with probability Tr(A_k^dagger A_k)/d and rescaled by its inverse square
  * root, so the mean of |amp|^2 is unbiased).  Trajectory t, channel c draws
- * the (t*2^32 + c + 1)-th SplitMix64 output of `seed`.
+ * the (t*2^32 + c + 1)-th SplitMix64 output of `seed`.  The draws are made on
+ * the host first; trajectories with the same picks on every channel have the
+ * same amplitudes, so each distinct pick sequence is contracted once and
+ * counted with its multiplicity (exact; tnq_plan_info reports how many were
+ * distinct).
  * bits: [n_bs][n] int8 host or device; p_out, stderr_out: [n_bs] double, host
  * or device (stderr_out may be NULL).  Errors as tnq_amplitudes. */
 tnq_status tnq_noisy_probabilities(tnq_ctx* ctx, tnq_plan* p, int64_t n_traj, uint64_t seed,
@@ -296,13 +302,18 @@ tnq_status tnq_contract_pair(tnq_ctx* ctx, const void* A, int ra, const int* a_l
  * device memory while they run, such as programs whose own pool allocator owns
  * all device memory, or latency-critical loops that cannot accept the device
  * synchronisation that freeing memory implies.  Its scratch is one static
- * device array of 64 MiB inside the library, held by every GPU that loads the
- * library until the process exits.  The first call on a device looks up that
- * array's address and should come before any stream capture.  All calls share
- * the array and it keeps the last call's contents, so calls that overlap on
- * the GPU race.  Errors: INVALID_ARG when the contraction needs more than 64 MiB
- * of scratch (see tnq_contract_workspace_bytes) or the labels are inconsistent;
- * TIMEOUT, CUDA as tnq_contract_pair. */
+ * device array of 64 MiB inside the library.  With CUDA's lazy module loading
+ * (the default) the array is committed on a device by the first call there,
+ * which looks up its address, and it stays until the process exits; a caller
+ * whose own pool takes all device memory must make that first call before
+ * the pool reserves it, and the first call should come before any stream
+ * capture.  A call returns after the contraction has completed (it
+ * synchronizes the context's stream), and the context's per-kernel timing
+ * records are not taken for it.  All calls share the array and it keeps the
+ * last call's contents, so calls that overlap on the GPU race.  Errors:
+ * INVALID_ARG when the contraction needs more than 64 MiB of scratch (see
+ * tnq_contract_workspace_bytes) or the labels are inconsistent; TIMEOUT, CUDA
+ * as tnq_contract_pair. */
 tnq_status tnq_contract_pair_noalloc(tnq_ctx* ctx, const void* A, int ra, const int* a_labels, const void* B,
                                      int rb, const int* b_labels, void* C, int rc, const int* c_labels);
 

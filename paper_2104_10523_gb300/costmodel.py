@@ -25,19 +25,20 @@ import numpy as np
 from . import tnq
 
 
-def circuit_flops(circ, n_candidates=8, seed=0):
-    p = tnq.Plan(tnq.Circuit(circ), batch_log2=0, path_mode=tnq.TNQ_PATH_BEST, n_candidates=n_candidates,
-                 seed=seed)
+def circuit_flops(circ, n_candidates=8, seed=0, path_mode=tnq.TNQ_PATH_BEST):
+    p = tnq.Plan(tnq.Circuit(circ), batch_log2=0, path_mode=path_mode, n_candidates=n_candidates, seed=seed)
     return p.info["flops_per_batch"]
 
 
-def pick_circuits(seeds, max_flops, make):
+def pick_circuits(seeds, max_flops, make, quick=False):
     """Circuits of the workload whose flop-minimal plan stays within max_flops
-    (the rest are too expensive to time repeatedly)."""
+    (the rest are too expensive to time repeatedly).  quick: judge by one
+    bisection candidate instead of eight (an upper bound, much faster)."""
     out = []
     for s in seeds:
         c = make(s)
-        if circuit_flops(c) <= max_flops:
+        f = circuit_flops(c, 1, path_mode=tnq.TNQ_PATH_BISECT) if quick else circuit_flops(c)
+        if f <= max_flops:
             out.append((s, c))
     return out
 
@@ -72,8 +73,13 @@ def step_rows(ctx, plan, bits, precision):
     for r in rec:
         if r[1] >= 0:
             ms[int(r[1])] += r[8]
-    us = np.maximum(ms / n_slices * 1e3, 1e-3)
-    return plan.features(precision), np.log(us).astype(np.float32)
+    # time of one run of a step: folded steps ran when the plan was bound (no
+    # row), slice-invariant and slice-batched steps once, the others per slice
+    st = plan.steps()
+    runs = np.where(st[:, 7] & (4 | 16), 1, n_slices)
+    keep = (st[:, 7] & 8) == 0
+    us = np.maximum(ms / runs * 1e3, 1e-3)
+    return plan.features(precision)[keep], np.log(us[keep]).astype(np.float32)
 
 
 def collect(ctx, circuits, per_circuit, precision, seed=0):
@@ -125,18 +131,32 @@ def main():
     ap.add_argument("--max-flops", type=float, default=2e10)
     ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--config5", action="store_true",
+                    help="the cost-model workload: training seeds 0-1999, held-out seeds 2000-2199, 32 candidates "
+                         "(circuits above --max-flops are left out)")
+    ap.add_argument("--save", default=None, help="write the trained parameters (float32 .npy) here")
     a = ap.parse_args()
     from workloads import cost_model_circuit
     t0 = time.time()
     ctx = tnq.Context(0, a.precision)
-    train_c = pick_circuits(range(0, 4 * a.train), a.max_flops, cost_model_circuit)[: a.train]
-    eval_c = pick_circuits(range(2000, 2000 + 4 * a.eval), a.max_flops, cost_model_circuit)[: a.eval]
+    if a.config5:
+        train_c = pick_circuits(range(0, 2000), a.max_flops, cost_model_circuit, quick=True)
+        eval_c = pick_circuits(range(2000, 2200), a.max_flops, cost_model_circuit, quick=True)
+        a.candidates = 32
+    else:
+        train_c = pick_circuits(range(0, 4 * a.train), a.max_flops, cost_model_circuit)[: a.train]
+        eval_c = pick_circuits(range(2000, 2000 + 4 * a.eval), a.max_flops, cost_model_circuit)[: a.eval]
+    t_pick = time.time() - t0
     X, t = collect(ctx, train_c, a.per_circuit, a.precision)
+    t_collect = time.time() - t0 - t_pick
     model = tnq.CostModel(ctx, hidden=256, max_batch=4096, seed=1)
     loss = model.train(X, t, epochs=a.epochs, batch=1024, lr=1e-3)
+    if a.save:
+        np.save(a.save, model.get_params())
     rows = evaluate(ctx, model, eval_c, n_candidates=a.candidates)
-    out = {"train_circuits": len(train_c), "train_rows": int(len(t)), "final_loss": loss,
-           "eval": summarize(rows), "seconds": time.time() - t0, "rows": rows}
+    out = {"train_circuits": len(train_c), "eval_circuits": len(eval_c), "train_rows": int(len(t)),
+           "final_loss": loss, "target_variance": float(np.var(t)), "eval": summarize(rows),
+           "seconds": {"pick": t_pick, "collect": t_collect, "total": time.time() - t0}, "rows": rows}
     print(json.dumps(out))
 
 

@@ -364,12 +364,13 @@ tnq_status tnq_plan_get_info(const tnq_plan* pp, tnq_plan_info* info) {
   // executed flops: slice-invariant steps once per batch, the rest per slice
   const double n_slices = std::ldexp(1.0, (int)p.slice_labels.size());
   double fb = 0;
-  for (const auto& s : p.steps) fb += s.invariant ? s.flops : s.flops * n_slices;
+  for (const auto& s : p.steps) fb += s.fold ? 0.0 : s.once() ? s.flops : s.flops * n_slices;
   info->flops_per_batch = fb;
   info->bytes_per_pass = p.cost.bytes;
   info->search_ms = p.search_ms;
   info->workspace_bytes = p.ws_total;
   info->n_open = (int)p.net.open_qubits.size();
+  info->distinct_trajectories = p.last_distinct;
   return TNQ_OK;
 }
 
@@ -387,7 +388,8 @@ tnq_status tnq_plan_get_steps(const tnq_plan* pp, int* rec) {
     r[4] = s.nM;
     r[5] = s.nN;
     r[6] = s.nK;
-    r[7] = (s.a < L ? 1 : 0) | (s.b < L ? 2 : 0) | (s.invariant ? 4 : 0);
+    r[7] = (s.a < L ? 1 : 0) | (s.b < L ? 2 : 0) | (s.invariant ? 4 : 0) | (s.fold ? 8 : 0) |
+           (s.sliced_batch ? 16 : 0);
   }
   return TNQ_OK;
 }
@@ -583,9 +585,16 @@ tnq_status tnq_plan_create_learned(tnq_ctx* c, tnq_cost_model* m, const tnq_circ
     std::vector<float> y(n);
     tnq_status s = mlp_predict(ctx, cm, f.data(), n, y.data());
     if (s != TNQ_OK) return s;
+    // a step's runs per batch: none when folded at bind, one when it runs
+    // once per batch, one per slice otherwise; per slice on average
+    const double ns = std::ldexp(1.0, (int)cand.slice_labels.size());
     double sum = 0;
-    for (float v : y) sum += std::exp(double(v));
-    *t = sum * 1e-3;  // milliseconds
+    for (int64_t i = 0; i < n; ++i) {
+      const Step& s = cand.steps[size_t(i)];
+      const double runs = s.fold ? 0.0 : s.once() ? 1.0 : ns;
+      sum += runs / ns * std::exp(double(y[size_t(i)]));
+    }
+    *t = sum * 1e-3;  // milliseconds per slice (the caller scales by the slice count)
     return TNQ_OK;
   };
   tnq_plan_opts o2 = *o;

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -402,13 +403,16 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
 }
 
 tnq_status run_step(Ctx* ctx, Plan* p, size_t si, int slice_id, char* ws, int choice) {
+  static const std::vector<int> kNoSlices;
   auto& s = p->steps[si];
   auto& ta = p->tensors[s.a];
   auto& tb = p->tensors[s.b];
   void* acc = s.out == p->root ? (void*)(ws + p->ws_acc) : nullptr;
   void* C = s.out == p->root ? nullptr : (void*)(ws + p->tensors[s.out].offset);
+  // a slice-batched step keeps the sliced indices: nothing is fixed to a slice
+  const std::vector<int>& sl = s.sliced_batch ? kNoSlices : p->slice_labels;
   return run_gemm_step(ctx, ws + ta.offset, ta.labels, s.perm_a, ws + tb.offset, tb.labels, s.perm_b, s.a_req,
-                       s.b_req, p->slice_labels, slice_id, s.nH, s.nM, s.nN, s.nK, ws + p->ws_scratch_a,
+                       s.b_req, sl, s.sliced_batch ? 0 : slice_id, s.nH, s.nM, s.nN, s.nK, ws + p->ws_scratch_a,
                        ws + p->ws_scratch_b, C, acc, reinterpret_cast<int*>(ws + p->ws_misc + 4),
                        ws + p->ws_partial, choice);
 }
@@ -432,7 +436,8 @@ tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws, bool first) {
   const bool tuned = p->tuned_precision == ctx->precision && p->kernel_choice.size() == p->steps.size();
   const bool forced = ctx->kernel_policy == TNQ_KERNELS_TENSOR_CORES;
   for (size_t si = 0; si < p->steps.size(); ++si) {
-    if (p->steps[si].invariant && !first) continue;
+    if (p->steps[si].fold) continue;  // contracted when the plan was bound
+    if (p->steps[si].once() && !first) continue;
     ctx->cur_step = (int)si;
     const int choice = forced ? forced_tc_choice(ctx, p->steps[si]) : tuned ? p->kernel_choice[si] : -1;
     tnq_status st = run_step(ctx, p, si, slice_id, ws, choice);
@@ -442,6 +447,25 @@ tnq_status run_pass(Ctx* ctx, Plan* p, int slice_id, char* ws, bool first) {
   return TNQ_OK;
 }
 
+
+// Contract the plan's constant subtrees (steps whose leaves are all static)
+// once for the context's precision; their outputs persist in the workspace.
+tnq_status ensure_folded(Ctx* ctx, Plan* p) {
+  if (p->folded_precision == ctx->precision) return TNQ_OK;
+  char* ws = static_cast<char*>(p->bound_ws);
+  const bool tuned = p->tuned_precision == ctx->precision && p->kernel_choice.size() == p->steps.size();
+  const bool forced = ctx->kernel_policy == TNQ_KERNELS_TENSOR_CORES;
+  for (size_t si = 0; si < p->steps.size(); ++si) {
+    if (!p->steps[si].fold) continue;
+    ctx->cur_step = (int)si;
+    const int choice = forced ? forced_tc_choice(ctx, p->steps[si]) : tuned ? p->kernel_choice[si] : -1;
+    tnq_status st = run_step(ctx, p, si, 0, ws, choice);
+    if (st != TNQ_OK) return st;
+  }
+  ctx->cur_step = -1;
+  p->folded_precision = ctx->precision;
+  return TNQ_OK;
+}
 
 }  // namespace
 
@@ -571,6 +595,7 @@ tnq_status exec_bind(Ctx* ctx, Plan* p, void* ws, size_t bytes) {
   }
   p->bound_ws = ws;
   p->bound_bytes = bytes;
+  p->folded_precision = -1;
   return TNQ_OK;
 }
 
@@ -609,6 +634,10 @@ tnq_status exec_amplitudes_range(Ctx* ctx, Plan* p, int64_t n_bs, const int8_t* 
     return fail(TNQ_ERR_INVALID_ARG, "slice range outside [0, 2^n_sliced)");
   // the captured graph covers every slice; partial ranges launch directly
   const bool graphs = ctx->use_graphs && !ctx->timing && slice_begin == 0 && slice_count == n_slices;
+  {
+    tnq_status st = ensure_folded(ctx, p);
+    if (st != TNQ_OK) return st;
+  }
   for (int64_t base = 0; base < n_bs; base += per) {
     int64_t nv = std::min<int64_t>(per, n_bs - base);
     const size_t out_bytes = size_t(nv * n_out * vals) * 8;
@@ -725,6 +754,7 @@ tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda) {
   if (herr) return fail(TNQ_ERR_TIMEOUT, "a tensor-core GEMM wait expired during autotuning");
   p->kernel_choice = choice;
   p->tuned_precision = ctx->precision;
+  p->folded_precision = -1;  // the timing runs overwrote the folded outputs
   plan_release_graph(p);
   if (n_tc) *n_tc = ntc;
   if (n_cuda) *n_cuda = ncc;
@@ -733,12 +763,60 @@ tnq_status exec_autotune(Ctx* ctx, Plan* p, int reps, int* n_tc, int* n_cuda) {
 
 namespace {
 
+// SplitMix64 (Steele, Lea & Flood 2014) on the host: the uniform in [0, 1)
+// of trajectory t, channel c, the same draw the trajectory kernel makes.
+double host_uniform(uint64_t seed, uint64_t traj, uint64_t chan) {
+  const uint64_t i = (traj << 32) + chan + 1;
+  uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return double(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Distinct trajectories among 0 .. n_traj - 1: every channel's pick drawn as
+// on the device, equal pick vectors grouped (in order of first appearance)
+// with their multiplicities.  The mean of |amp|^2 over all trajectories is the
+// multiplicity-weighted mean over the distinct ones, exactly.
+void distinct_trajectories(const Plan* p, uint64_t seed, int64_t n_traj, std::vector<int8_t>* picks,
+                           std::vector<double>* mult) {
+  const size_t nch = p->chan_cumq.size();
+  std::map<std::vector<int8_t>, size_t> index;
+  std::vector<int8_t> v(nch);
+  picks->clear();
+  mult->clear();
+  for (int64_t t = 0; t < n_traj; ++t) {
+    for (size_t c = 0; c < nch; ++c) {
+      const auto& cq = p->chan_cumq[c];
+      const double u = host_uniform(seed, uint64_t(t), uint64_t(c));
+      int k = (int)cq.size() - 1;
+      for (int j = 0; j < (int)cq.size(); ++j)
+        if (u < cq[j]) {
+          k = j;
+          break;
+        }
+      v[c] = int8_t(k);
+    }
+    auto it = index.find(v);
+    if (it == index.end()) {
+      index.emplace(v, mult->size());
+      picks->insert(picks->end(), v.begin(), v.end());
+      mult->push_back(1.0);
+    } else {
+      (*mult)[it->second] += 1.0;
+    }
+  }
+}
+
 // Shared driver of the noisy calls: for every batch of bitstrings and every
 // chunk of 2^traj_log2 trajectories, build the trajectory leaves, contract all
 // slices into the FP64 accumulator, then hand the accumulator to `consume`.
+// With `distinct` (host picks [n_units][n_channels] and multiplicities) the
+// chunks run over those distinct trajectories instead of drawing on the GPU.
 template <typename Consume, typename BatchEnd>
 tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, uint64_t seed, int64_t n_bs,
-                        const int8_t* bits, Consume consume, BatchEnd batch_end) {
+                        const int8_t* bits, Consume consume, BatchEnd batch_end,
+                        const std::vector<int8_t>* distinct = nullptr, const std::vector<double>* mult = nullptr) {
   char* ws = static_cast<char*>(p->bound_ws);
   const int n = p->net.row_len, w = p->batch_log2, t = p->traj_log2;
   const int64_t per = int64_t(1) << w, tper = int64_t(1) << t;
@@ -755,6 +833,10 @@ tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, u
   TNQ_CUDA(cudaMemsetAsync(err_flag, 0, 2 * sizeof(int), ctx->stream));
   const size_t acc_bytes = 16 * (size_t(1) << p->tensors[p->root].rank);
   const int n_slices = 1 << p->slice_labels.size();
+  {
+    tnq_status st = ensure_folded(ctx, p);
+    if (st != TNQ_OK) return st;
+  }
   for (int64_t base = 0; base < n_bs; base += per) {
     const int64_t nv = std::min<int64_t>(per, n_bs - base);
     const int8_t* bsrc;
@@ -767,13 +849,29 @@ tnq_status noisy_driver(Ctx* ctx, Plan* p, int64_t traj_begin, int64_t n_traj, u
     TNQ_CUDA(fill_projections(ctx, pl, w, bsrc, nv, err_flag));
     tnq_status st = consume(-1, base, nv, 0, 0, bpos, tpos);  // batch start
     if (st != TNQ_OK) return st;
-    for (int64_t tb = 0; tb < n_traj; tb += tper) {
-      const int64_t nt = std::min<int64_t>(tper, n_traj - tb);
-      TNQ_CUDA(launch_traj_leaves(reinterpret_cast<const TrajLeafDesc*>(ws + p->ws_traj), (int)p->traj_leaves.size(),
-                                  reinterpret_cast<const TrajFactor*>(ws + p->ws_traj_factors),
-                                  reinterpret_cast<const double2*>(ws + p->ws_traj_mats),
-                                  reinterpret_cast<const double*>(ws + p->ws_traj_cumq), ws, seed,
-                                  uint64_t(traj_begin + tb), t, ctx->stream));
+    const int64_t units = distinct ? int64_t(mult->size()) : n_traj;
+    const size_t nch = p->chan_cumq.size();
+    for (int64_t tb = 0; tb < units; tb += tper) {
+      const int64_t nt = std::min<int64_t>(tper, units - tb);
+      if (distinct) {
+        TNQ_CUDA(cudaMemcpyAsync(ws + p->ws_dedup_picks, distinct->data() + size_t(tb) * nch, size_t(nt) * nch,
+                                 cudaMemcpyHostToDevice, ctx->stream));
+        TNQ_CUDA(cudaMemcpyAsync(ws + p->ws_dedup_w, mult->data() + tb, size_t(nt) * 8, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+        TNQ_CUDA(launch_traj_leaves(reinterpret_cast<const TrajLeafDesc*>(ws + p->ws_traj),
+                                    (int)p->traj_leaves.size(),
+                                    reinterpret_cast<const TrajFactor*>(ws + p->ws_traj_factors),
+                                    reinterpret_cast<const double2*>(ws + p->ws_traj_mats),
+                                    reinterpret_cast<const double*>(ws + p->ws_traj_cumq), ws, seed, 0, t, ctx->stream,
+                                    reinterpret_cast<const int8_t*>(ws + p->ws_dedup_picks), int(nch), nt));
+      } else {
+        TNQ_CUDA(launch_traj_leaves(reinterpret_cast<const TrajLeafDesc*>(ws + p->ws_traj),
+                                    (int)p->traj_leaves.size(),
+                                    reinterpret_cast<const TrajFactor*>(ws + p->ws_traj_factors),
+                                    reinterpret_cast<const double2*>(ws + p->ws_traj_mats),
+                                    reinterpret_cast<const double*>(ws + p->ws_traj_cumq), ws, seed,
+                                    uint64_t(traj_begin + tb), t, ctx->stream));
+      }
       ctx->launches++;
       TNQ_CUDA(launch_zero(ws + p->ws_acc, acc_bytes, ctx->stream));
       for (int s = 0; s < n_slices; ++s) {
@@ -828,7 +926,8 @@ tnq_status exec_noisy(Ctx* ctx, Plan* p, int64_t n_traj, uint64_t seed, int64_t 
       return TNQ_OK;
     }
     TNQ_CUDA(launch_noisy_accumulate(ws + p->ws_acc, nv, nt, bpos.data(), (int)bpos.size(), tpos.data(),
-                                     (int)tpos.size(), psum, p2sum, ctx->stream));
+                                     (int)tpos.size(), psum, p2sum, ctx->stream,
+                                     reinterpret_cast<const double*>(ws + p->ws_dedup_w)));
     ctx->launches++;
     return TNQ_OK;
   };
@@ -843,7 +942,16 @@ tnq_status exec_noisy(Ctx* ctx, Plan* p, int64_t n_traj, uint64_t seed, int64_t 
     if (!p_dev || (se_out && !se_dev)) TNQ_CUDA(cudaStreamSynchronize(ctx->stream));
     return TNQ_OK;
   };
-  return noisy_driver(ctx, p, 0, n_traj, seed, n_bs, bits, consume, batch_end);
+  // identical trajectories (most draws pick the identity-like operator A_0)
+  // are contracted once and weighted by their number
+  // (the draws of the last (seed, n_traj) are kept with the plan)
+  if (p->dedup_seed != seed || p->dedup_n != n_traj || p->dedup_mult.empty()) {
+    distinct_trajectories(p, seed, n_traj, &p->dedup_picks, &p->dedup_mult);
+    p->dedup_seed = seed;
+    p->dedup_n = n_traj;
+  }
+  p->last_distinct = (int64_t)p->dedup_mult.size();
+  return noisy_driver(ctx, p, 0, n_traj, seed, n_bs, bits, consume, batch_end, &p->dedup_picks, &p->dedup_mult);
 }
 
 tnq_status exec_traj_amplitudes(Ctx* ctx, Plan* p, uint64_t seed, int64_t traj_begin, int64_t n_traj, int64_t n_bs,
@@ -902,6 +1010,10 @@ tnq_status exec_expectation(Ctx* ctx, Plan* p, const double* coeffs, double* val
   // <0...0| closes every wire (the network is U, the Pauli operators, U^dagger)
   TNQ_CUDA(cudaMemsetAsync(bits_stage, 0, size_t(p->net.row_len), ctx->stream));
   TNQ_CUDA(fill_projections(ctx, proj_leaves(p, ws), 0, bits_stage, 1, err_flag));
+  {
+    tnq_status st = ensure_folded(ctx, p);
+    if (st != TNQ_OK) return st;
+  }
   std::vector<double> vals(size_t(p->n_terms));
   std::vector<double2> host(static_cast<size_t>(tper));
   // without selectors (every term the identity) one contraction serves all terms

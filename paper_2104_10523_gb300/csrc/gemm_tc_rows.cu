@@ -29,9 +29,9 @@
 // parts), which lets TF32 rows of K = 64 (four atoms per part) run beside a
 // 128 KB expanded small operand.
 //
-// In the split modes the product hi*hi accumulates into one TMEM buffer and
-// the two correction products hi*lo, lo*hi into a second one; the epilogue
-// adds them in FP32 registers.  The tensor-memory accumulator adds each MMA's
+// In the TF32 split mode the product hi*hi accumulates into one TMEM buffer
+// and the two correction products hi*lo, lo*hi into a second one; the
+// epilogue adds them in FP32 registers.  The tensor-memory accumulator adds each MMA's
 // result with truncation toward zero, so a chain of additions into the large
 // accumulator shrinks it by about half an ulp per addition; keeping the
 // corrections (about 2^-9 of it) apart cuts that chain to one addition per K
@@ -582,7 +582,10 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   P.nks_part = P.kparts == 1 ? P.nks : 4 * P.patoms;  // parts of several atoms hold whole atoms of K
   P.kc = P.kparts == 1 ? K : P.patoms * TR_ROW_BYTES / (2 * (P.kind_bf16 ? 2 : 4));
   P.nacc = P.npad <= 64 ? 4 : 2;  // TMEM: acc_cols * nacc <= 512 columns
-  P.dual = (P.split && P.npad <= 128) ? 1 : 0;
+  // TF32x3 sums are FP32-accurate except for the truncating accumulation, so
+  // they take the separate correction buffer; BF16x3 errors are dominated by
+  // its 16-bit operand split, where the extra TMEM reads buy nothing
+  P.dual = (P.split && !P.kind_bf16 && P.npad <= 128) ? 1 : 0;
   P.acc_cols = P.npad * (P.dual ? 2 : 1);
   const int ch = P.kc <= 8 ? 8 : 16;
   P.nchunks = (P.kc + ch - 1) / ch;

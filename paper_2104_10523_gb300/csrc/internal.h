@@ -131,7 +131,16 @@ struct Step {
   // no sliced label in the step's subtree: its result is the same for every
   // slice, so a batch computes it in its first slice only
   bool invariant = false;
+  // subtree of static leaves only (no projection, trajectory or sliced index):
+  // a constant of the circuit, contracted once when the plan is bound
+  bool fold = false;
+  // small slice-dependent subtree that keeps its sliced indices as batch
+  // indices: one run per batch gives every slice's result at once, and the
+  // per-slice steps that read it pick their slice like they do from a leaf
+  bool sliced_batch = false;
   double flops = 0;
+  // runs once per batch (in its first slice) rather than once per slice
+  bool once() const { return invariant || sliced_batch; }
 };
 
 struct TensorSlot {
@@ -152,6 +161,7 @@ struct Plan {
   TreeCost cost;
   double search_ms = 0;
   int batch_log2 = 0, traj_log2 = 0;
+  int cap_log2 = 31;              // max_intermediate_log2 the plan was made for
   int root = -1;
   // doubled density-matrix network (Sec. 3.3): results are the real numbers
   // <<x, x|rho>> = p(x), written as one double per bitstring
@@ -180,6 +190,17 @@ struct Plan {
   std::vector<cd> traj_mats;      // 16 entries per matrix (2x2 use stride 2)
   std::vector<double> traj_cumq;
   size_t ws_traj = 0, ws_traj_factors = 0, ws_traj_mats = 0, ws_traj_cumq = 0;
+  // cumulative Kraus probabilities per channel (by channel index), for the
+  // host draws that find the distinct trajectories of an estimate, and the
+  // workspace of one pass of distinct trajectories: picks [2^t][n_channels]
+  // and their multiplicities [2^t]
+  std::vector<std::vector<double>> chan_cumq;
+  size_t ws_dedup_picks = 0, ws_dedup_w = 0;
+  int64_t last_distinct = 0;      // distinct trajectories of the last noisy estimate
+  uint64_t dedup_seed = 0;        // draws of the last estimate: seed, count, distinct picks
+  int64_t dedup_n = -1;
+  std::vector<int8_t> dedup_picks;
+  std::vector<double> dedup_mult;
   int max_operand_log2 = 0;
   // candidate trees examined by the search: sliced flops per batch, predicted
   // time (learned ranking, else -1), the flop-minimal one and the chosen one
@@ -199,6 +220,8 @@ struct Plan {
   void* bound_ws = nullptr;
   size_t bound_bytes = 0;
   int bound_precision = -1;
+  // precision the folded (constant) steps were last contracted in; -1 = stale
+  int folded_precision = -1;
 };
 
 // Shape of the network a plan contracts beyond the plain amplitude network:

@@ -32,7 +32,14 @@ void build_perm_desc(const int* src_labels, int src_rank, const int* dst_labels,
   };
   std::vector<int> s_of_d(dst_rank);
   for (int p = 0; p < dst_rank; ++p) s_of_d[p] = src_pos(dst_labels[p]);
-  for (int j = 0; j < n_slice; ++j) d->slice_src[j] = src_pos(slice_labels[j]);
+  // a sliced label fixes its source bit to the slice's value, unless the
+  // destination keeps it as an index of its own
+  auto in_dst = [&](int l) {
+    for (int p = 0; p < dst_rank; ++p)
+      if (dst_labels[p] == l) return true;
+    return false;
+  };
+  for (int j = 0; j < n_slice; ++j) d->slice_src[j] = in_dst(slice_labels[j]) ? -1 : src_pos(slice_labels[j]);
   for (int j = n_slice; j < 32; ++j) d->slice_src[j] = -1;
   // tile: lowest destination bits and lowest source bits, grown until 11 bits
   int target = std::min(dst_rank, 11);

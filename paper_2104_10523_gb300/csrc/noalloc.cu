@@ -9,11 +9,19 @@
 // array of fixed size that is part of the loaded library.
 //
 // Facts a caller must know:
-//   * every GPU that loads the library holds the array (kNoAllocScratchBytes)
-//     until the process exits;
+//   * the array (kNoAllocScratchBytes) is device memory of the library's
+//     module on each GPU; with CUDA's lazy module loading (the default) the
+//     module, and so the array, is committed on a device when the first call
+//     there looks the array up, and it stays until the process exits.  A
+//     caller whose own pool takes all device memory must make that first call
+//     before the pool reserves it;
 //   * the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress with that device current) and caches it; make that
 //     first call before any stream capture;
+//   * a call returns after its contraction has completed (it reads the error
+//     flag back and synchronizes the context's stream);
+//   * the context's per-kernel timing records (tnq_ctx_set_timing) are not
+//     taken for these calls;
 //   * all calls share the array and it keeps the last call's contents: calls
 //     that overlap on the GPU (different streams, threads or contexts without
 //     ordering between them) race on it and give wrong results;

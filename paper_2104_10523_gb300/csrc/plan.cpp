@@ -17,6 +17,8 @@
 #include <map>
 #include <random>
 
+#include <set>
+
 #include "internal.h"
 #include "splitk.h"
 #include "gemm_tc.cuh"
@@ -25,6 +27,9 @@
 namespace tnq {
 
 namespace {
+
+// Largest slice-batched output (log2 elements, sliced indices included).
+constexpr int kSliceBatchMaxLog2 = 16;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -42,6 +47,49 @@ void layout_steps(Plan* p) {
     ts.leaf = true;
     ts.labels = p->net.leaves[i].labels;  // storage order, may include sliced labels
     ts.rank = (int)ts.labels.size();
+  }
+  // ---- classes of the steps: folded (constant subtree), slice-batched (small
+  // slice-dependent subtree run once with its sliced indices kept), or
+  // neither.  A tensor's "sliced count" is the number of distinct sliced
+  // indices in its subtree; an unsliced subtree result has the rank of its
+  // open indices.
+  const int NT = L + (int)t.nodes.size();
+  std::vector<std::set<int>> sub_sliced(NT);
+  std::vector<char> is_const(NT, 0), is_batched(NT, 0);
+  std::vector<int> open_rank(NT, 0);
+  {
+    std::vector<std::map<int, int>> c2(NT);
+    for (int i = 0; i < L; ++i) {
+      const Leaf& lf = p->net.leaves[i];
+      is_const[i] = lf.kind == LEAF_STATIC;
+      for (int l : lf.labels) {
+        if (p->sliced[l]) {
+          sub_sliced[i].insert(l);
+          is_const[i] = 0;
+        } else {
+          c2[i][l] = 1;
+        }
+      }
+      open_rank[i] = (int)c2[i].size();
+    }
+    for (int j = 0; j < (int)t.nodes.size(); ++j) {
+      const int x = t.nodes[j].first, y = t.nodes[j].second, id = L + j;
+      for (auto& e : c2[x]) c2[id][e.first] += e.second;
+      for (auto& e : c2[y]) c2[id][e.first] += e.second;
+      int r = 0;
+      for (auto& e : c2[id])
+        if (h.is_output[e.first] || e.second < h.label_count[e.first]) ++r;
+      open_rank[id] = r;
+      c2[x].clear();
+      c2[y].clear();
+      sub_sliced[id] = sub_sliced[x];
+      sub_sliced[id].insert(sub_sliced[y].begin(), sub_sliced[y].end());
+      is_const[id] = is_const[x] && is_const[y];
+      // children must be leaves, slice-free steps or slice-batched steps
+      auto ready = [&](int c) { return c < L || sub_sliced[c].empty() || is_batched[c]; };
+      is_batched[id] = !sub_sliced[id].empty() && id != L + (int)t.nodes.size() - 1 && ready(x) && ready(y) &&
+                       open_rank[id] + (int)sub_sliced[id].size() <= std::min(kSliceBatchMaxLog2, p->cap_log2);
+    }
   }
   // subtree label counts for open/closed decisions
   std::vector<std::map<int, int>> cnt(L + t.nodes.size());
@@ -63,7 +111,12 @@ void layout_steps(Plan* p) {
     std::vector<int> out_set;
     for (auto& e : cnt[id])
       if (h.is_output[e.first] || e.second < h.label_count[e.first]) out_set.push_back(e.first);
-    std::vector<int> lx = eff(x), ly = eff(y);
+    // a slice-batched step keeps every sliced index of its operands (as a
+    // batch index when both hold it)
+    std::vector<int> lx = is_batched[id] ? p->tensors[x].labels : eff(x);
+    std::vector<int> ly = is_batched[id] ? p->tensors[y].labels : eff(y);
+    if (is_batched[id])
+      for (int l : sub_sliced[id]) out_set.push_back(l);
     // A = operand with fewer elements (it is the one expanded for the tensor cores)
     bool x_is_a = lx.size() <= ly.size();
     int a = x_is_a ? x : y, b = x_is_a ? y : x;
@@ -118,6 +171,8 @@ void layout_steps(Plan* p) {
     s.perm_a = p->tensors[a].labels != s.a_req;
     s.perm_b = p->tensors[b].labels != s.b_req;
     s.flops = 8.0 * std::ldexp(1.0, s.nH + s.nM + s.nN + s.nK);
+    s.fold = is_const[id];
+    s.sliced_batch = is_batched[id];
     auto& ts = p->tensors[id];
     ts.labels = s.out_labels;
     ts.rank = (int)s.out_labels.size();
@@ -138,13 +193,17 @@ void layout_steps(Plan* p) {
     dep[s.out] = dep[s.a] || dep[s.b];
     s.invariant = !dep[s.out];
   }
-  // invariant outputs consumed by a slice-dependent step persist for the batch
+  // lifetime class of a step: 0 folded (at bind), 1 once per batch, 2 per
+  // slice; an output read by a step of a later class persists outside the
+  // reusable arena (folded outputs for the binding, the others for the batch)
+  auto cls = [&](const Step& s) { return s.fold ? 0 : s.once() ? 1 : 2; };
+  std::vector<int> out_cls(p->tensors.size(), -1);
+  for (auto& s : p->steps) out_cls[s.out] = cls(s);
   std::vector<char> pinned(p->tensors.size(), 0);
-  for (auto& s : p->steps)
-    if (!s.invariant) {
-      if (s.a >= L && !dep[s.a]) pinned[s.a] = 1;
-      if (s.b >= L && !dep[s.b]) pinned[s.b] = 1;
-    }
+  for (auto& s : p->steps) {
+    if (s.a >= L && out_cls[s.a] < cls(s)) pinned[s.a] = 1;
+    if (s.b >= L && out_cls[s.b] < cls(s)) pinned[s.b] = 1;
+  }
 
   // ---- workspace: [leaves][arena of intermediates][scratch A][scratch B][acc][misc]
   size_t off = 0;
@@ -231,6 +290,10 @@ void layout_steps(Plan* p) {
   off = align_up(off + 16 * p->traj_mats.size(), 256);
   p->ws_traj_cumq = off;
   off = align_up(off + 8 * p->traj_cumq.size(), 256);
+  p->ws_dedup_picks = off;
+  off = align_up(off + (p->chan_cumq.size() << p->traj_log2), 256);
+  p->ws_dedup_w = off;
+  off = align_up(off + (p->chan_cumq.empty() ? 0 : size_t(8) << p->traj_log2), 256);
   p->ws_misc = off;
   const size_t per = size_t(1) << p->batch_log2;
   const size_t n_open = p->net.open_qubits.size();
@@ -253,6 +316,12 @@ static void build_traj_program(const Circuit& c, Plan* p) {
   p->traj_factors.clear();
   p->traj_mats.clear();
   p->traj_cumq.clear();
+  p->chan_cumq.assign(c.n_channels, {});
+  for (const COp& op : c.ops)
+    if (op.channel && !op.selector && op.channel_index >= 0) {
+      double acc = 0;
+      for (double q : op.kraus_q) p->chan_cumq[op.channel_index].push_back(acc += q);
+    }
   auto push_mat = [&](const std::vector<cd>& m) {
     int idx = (int)(p->traj_mats.size() / 16);
     std::vector<cd> e(16, cd(0, 0));
@@ -361,6 +430,7 @@ tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, c
   if (o.max_intermediate_log2 < 1 || o.max_intermediate_log2 > 31)
     return fail(TNQ_ERR_INVALID_ARG, "max_intermediate_log2 must be in [1, 31]");
   p->batch_log2 = o.batch_log2;
+  p->cap_log2 = o.max_intermediate_log2;
   p->traj_log2 = (c.n_channels > 0 || c.n_selectors > 0) ? o.traj_log2 : 0;
   tnq_status st = build_network(c, p->batch_log2, p->traj_log2, spec.open, spec.row_len, &p->net);
   if (st != TNQ_OK) return st;
@@ -458,6 +528,7 @@ tnq_status make_plan_ranked(const Circuit& c, const tnq_plan_opts& o, Plan* p, c
       tmp.hyper = p->hyper;
       tmp.tree = cands[i];
       tmp.batch_log2 = p->batch_log2;
+      tmp.cap_log2 = p->cap_log2;
       tmp.traj_log2 = p->traj_log2;
       tmp.sliced.assign(h.n_labels, 0);
       tmp.slice_labels = slices[i];

@@ -42,7 +42,8 @@ __global__ void traj_leaf_kernel(const TrajLeafDesc* __restrict__ leaves, int n_
     for (int f = 0; f < L.n_factors; ++f) {
       const TrajFactor F = factors[L.factor_off + f];
       int mi = F.mat_off;
-      if (F.channel == 2) {
+      if (F.channel == 2 || (F.channel == 1 && picks)) {
+        // pick table: per term (observables) or per distinct trajectory (noise)
         const int64_t term = int64_t(traj_base) + tau;
         mi += term < n_terms ? int(picks[term * n_sel + F.chan_index]) : 0;
       } else if (F.channel) {
@@ -116,15 +117,16 @@ __device__ __forceinline__ size_t scatter(long long v, const Pos& P) {
 }
 
 __global__ void noisy_accumulate_kernel(const double2* __restrict__ acc, int64_t nb, int64_t nt, Pos bp, Pos tp,
-                                        double* psum, double* p2sum) {
+                                        double* psum, double* p2sum, const double* __restrict__ weights) {
   for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < nb; b += int64_t(gridDim.x) * blockDim.x) {
     const size_t base = scatter(b, bp);
     double s = 0.0, s2 = 0.0;
     for (int64_t t = 0; t < nt; ++t) {
       const double2 a = acc[base | scatter(t, tp)];
       const double p = a.x * a.x + a.y * a.y;
-      s += p;
-      s2 += p * p;
+      const double w = weights ? weights[t] : 1.0;
+      s += w * p;
+      s2 += w * p * p;
     }
     psum[b] += s;
     p2sum[b] += s2;
@@ -175,9 +177,11 @@ cudaError_t launch_traj_leaves(const TrajLeafDesc* leaves, int n_leaves, const T
 }
 
 cudaError_t launch_noisy_accumulate(const void* acc, int64_t nb, int64_t nt, const int* bpos, int nbpos,
-                                    const int* tpos, int ntpos, double* psum, double* p2sum, cudaStream_t st) {
+                                    const int* tpos, int ntpos, double* psum, double* p2sum, cudaStream_t st,
+                                    const double* weights) {
   noisy_accumulate_kernel<<<blocks_for(nb), 256, 0, st>>>(reinterpret_cast<const double2*>(acc), nb, nt,
-                                                          make_pos(bpos, nbpos), make_pos(tpos, ntpos), psum, p2sum);
+                                                          make_pos(bpos, nbpos), make_pos(tpos, ntpos), psum, p2sum,
+                                                          weights);
   return cudaGetLastError();
 }
 

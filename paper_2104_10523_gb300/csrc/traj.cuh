@@ -41,16 +41,20 @@ struct TrajLeafDesc {
 // factors name (each matrix takes 16 entries); cumq: cumulative probabilities.
 // Selector factors of trajectory (term) t use matrix mat_off + picks[t * n_sel
 // + chan_index] (picks: device int8 [n_terms][n_sel]; terms t >= n_terms, the
-// padding of a last pass, take pick 0).
+// padding of a last pass, take pick 0).  With a pick table, Kraus channels
+// take their pick from it as well (the distinct trajectories of a noisy
+// estimate, drawn on the host) instead of drawing it.
 cudaError_t launch_traj_leaves(const TrajLeafDesc* leaves, int n_leaves, const TrajFactor* factors,
                                const double2* mats, const double* cumq, char* ws, uint64_t seed,
                                uint64_t traj_base, int traj_log2, cudaStream_t st, const int8_t* picks = nullptr,
                                int n_sel = 0, int64_t n_terms = 0);
 
-// For b < nb: psum[b] += sum_{t < nt} |amp(b, t)|^2, p2sum[b] += sum_t |amp|^4, with
-// amp(b, t) = acc[pdep(b, bpos) | pdep(t, tpos)] (FP64, trajectories in order).
+// For b < nb: psum[b] += sum_{t < nt} w_t |amp(b, t)|^2, p2sum[b] += sum_t w_t |amp|^4,
+// with amp(b, t) = acc[pdep(b, bpos) | pdep(t, tpos)] (FP64, trajectories in
+// order) and w_t = weights[t] (device; NULL: every weight 1).
 cudaError_t launch_noisy_accumulate(const void* acc, int64_t nb, int64_t nt, const int* bpos, int nbpos,
-                                    const int* tpos, int ntpos, double* psum, double* p2sum, cudaStream_t st);
+                                    const int* tpos, int ntpos, double* psum, double* p2sum, cudaStream_t st,
+                                    const double* weights = nullptr);
 
 // p[b] = psum[b] / n, se[b] = sqrt(max(p2sum/n - p^2, 0) / (n - 1)) (se optional).
 cudaError_t launch_noisy_finalize(const double* psum, const double* p2sum, int64_t nb, int64_t n_traj, double* p,

@@ -59,7 +59,7 @@ class TnqPlanInfo(C.Structure):
     _fields_ = [("n_leaves", C.c_int), ("n_steps", C.c_int), ("n_sliced", C.c_int), ("max_log2", C.c_int),
                 ("batch_log2", C.c_int), ("traj_log2", C.c_int), ("flops_per_pass", C.c_double),
                 ("flops_per_batch", C.c_double), ("bytes_per_pass", C.c_double), ("search_ms", C.c_double),
-                ("workspace_bytes", C.c_size_t), ("n_open", C.c_int)]
+                ("workspace_bytes", C.c_size_t), ("n_open", C.c_int), ("distinct_trajectories", C.c_int64)]
 
 
 class TnqError(RuntimeError):

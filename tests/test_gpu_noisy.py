@@ -118,3 +118,25 @@ def test_full_noisy_workload_sampled_trajectories(T):
     assert np.all(p >= 0) and np.all(np.isfinite(se))
     # mean of 2^n p over uniform bitstrings is ~1 for a scrambling circuit (loose sanity)
     assert 0.5 < p.mean() * 2 ** 20 < 1.5
+
+
+def test_distinct_trajectories_counted_once(T):
+    """Most trajectories of a weakly noisy circuit draw A_0 on every channel;
+    the estimate contracts each distinct pick sequence once with its
+    multiplicity, which leaves the estimate equal (to rounding) to the mean
+    over the individual trajectories."""
+    circ = noisy_grid_circuit(2, 3, 4, seed=2, p_depol=0.01, gamma=0.01)
+    bits = random_bitstrings(6, 8, 4)
+    ctx, plan = setup(T, circ, 3, 4, path_mode=0)
+    n_traj, seed = 256, 77
+    p, se = ctx.noisy_probabilities(plan, bits, n_traj, seed)
+    distinct = T.tnq_plan_get_info(plan.h)["distinct_trajectories"]
+    picks = [tuple(onoise.trajectory_picks(circ, seed, t)) for t in range(n_traj)]
+    assert distinct == len(set(picks)) and distinct < n_traj // 2
+    amps = ctx.trajectory_amplitudes(plan, bits, seed, 0, n_traj)
+    mean = np.mean(np.abs(amps) ** 2, axis=0)
+    assert np.allclose(p, mean, rtol=1e-10, atol=1e-14)
+    m2 = np.mean(np.abs(amps) ** 4, axis=0)
+    se_ref = np.sqrt(np.maximum(m2 - mean ** 2, 0) / (n_traj - 1))
+    assert np.allclose(se, se_ref, rtol=1e-6, atol=1e-14)
+

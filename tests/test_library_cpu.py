@@ -60,17 +60,32 @@ def test_plan_step_accounting(mode, w):
     info = p.info
     st = p.steps()
     assert info["n_steps"] == info["n_leaves"] - 1
-    flops = sum(8.0 * 2.0 ** (r[3] + r[4] + r[5] + r[6]) for r in st)
-    assert math.isclose(flops, info["flops_per_pass"], rel_tol=1e-12)
-    # slice-invariant steps run once per batch, the rest once per slice
-    inv = [bool(r[7] & 4) for r in st]
     per = [8.0 * 2.0 ** (r[3] + r[4] + r[5] + r[6]) for r in st]
-    want = sum(f if i else f * 2 ** info["n_sliced"] for f, i in zip(per, inv))
-    assert math.isclose(info["flops_per_batch"], want, rel_tol=1e-12)
-    if info["n_sliced"] == 0:
-        assert all(inv)
+    inv = [bool(r[7] & 4) for r in st]
+    fold = [bool(r[7] & 8) for r in st]
+    batched = [bool(r[7] & 16) for r in st]
+    # a slice-batched step keeps its sliced indices, so only the others add
+    # up to the per-slice flops of the tree
+    plain = sum(f for f, b in zip(per, batched) if not b)
+    if not any(batched):
+        assert math.isclose(plain, info["flops_per_pass"], rel_tol=1e-12)
     else:
-        assert not inv[-1]  # the root holds every leaf, sliced ones included
+        assert plain < info["flops_per_pass"]
+    # folded steps run when the plan is bound, slice-invariant and slice-batched
+    # steps once per batch, the rest once per slice
+    want = sum(0.0 if fo else f if (i or b) else f * 2 ** info["n_sliced"]
+               for f, i, fo, b in zip(per, inv, fold, batched))
+    assert math.isclose(info["flops_per_batch"], want, rel_tol=1e-12)
+    assert not any(fo and b for fo, b in zip(fold, batched))
+    assert all(i for fo, i in zip(fold, inv) if fo)      # a constant subtree holds no sliced index
+    assert not any(i for b, i in zip(batched, inv) if b)  # a slice-batched one does
+    if info["n_sliced"] == 0:
+        assert all(inv) and not any(batched)
+    else:
+        assert not inv[-1] and not batched[-1]  # the root holds every leaf and adds into the slice sum
+    # with batch indices every projection leaf depends on the bitstrings, so
+    # the root never folds
+    assert not fold[-1]
 
     # GEMM shape consistency: a = K+M+H bits, b = K+N+H bits, out = N+M+H bits
     for r in st:
@@ -79,6 +94,17 @@ def test_plan_step_accounting(mode, w):
         assert r[2] == r[5] + r[4] + r[3]
     # the root holds exactly the batch bits
     assert st[-1][2] == w
+
+
+def test_folded_and_slice_batched_steps():
+    """A sliced plan of a deep circuit has constant subtrees (folded at bind)
+    and small slice-dependent subtrees that keep their sliced indices."""
+    p = _plan(grid_circuit(4, 4, 10, 5), max_intermediate_log2=9, batch_log2=2, path_mode=tnq.TNQ_PATH_GREEDY)
+    st = p.steps()
+    assert p.info["n_sliced"] >= 2
+    assert any(r[7] & 8 for r in st)
+    assert any(r[7] & 16 for r in st)
+    assert all(max(r[0], r[1], r[2]) <= 16 for r in st if r[7] & 16)
 
 
 def test_slicing_meets_cap():
