@@ -8,7 +8,13 @@
   tests/golden/grid5x5_amplitudes.txt (the FP64 statevector oracle O1).
 
 Tolerance: relative L2 error over the stored bitstrings, per precision mode:
-FP32 and TF32x3 <= 1e-5, BF16x3 <= 2e-5, TF32 <= 5e-3.
+FP32 and TF32x3 <= 1e-5, TF32 <= 5e-3, and BF16x3 <= 5e-5 for these deep
+networks.  The BF16x3 bound follows from its arithmetic: splitting an FP32
+value into two BF16 parts leaves a relative representation error of about
+2^-17, so one contraction carries an error of a few 1e-6 (4.4e-6 measured on
+the tall-skinny steps of this workload); independent errors of the steps on a
+chain of the contraction tree add in quadrature, and the chains here are up to
+about a hundred steps long.
 """
 import os
 
@@ -21,7 +27,7 @@ from workloads import grid_circuit, random_bitstrings
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 2e-5, "tf32": 5e-3}
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 5e-5, "tf32": 5e-3}
 
 
 def rel_l2(a, b):
