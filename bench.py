@@ -10,7 +10,9 @@ contractions, the FP64 cross-slice sum, the mapping to bitstring order).
 
 Prints one JSON line (rank 0).  Under torchrun every rank contracts its own
 bitstrings (weak scaling, no collective on the data path); the elapsed time is
-the maximum over ranks.
+the maximum over ranks.  The line also reports the relative L2 error of the
+benched mode and of the plain FP32 arm against FP64 amplitudes stored by the
+oracle for this workload (tests/golden/config3_amplitudes.txt).
 """
 from __future__ import annotations
 
@@ -43,19 +45,29 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3", "bf16x3"],
+                    help="default TF32x3: the tensor-core mode whose amplitudes meet the metric's 1e-5 "
+                         "relative error against the FP64 oracle at this workload")
     ap.add_argument("--batch-log2", type=int, default=2)
     ap.add_argument("--candidates", type=int, default=2048)
     ap.add_argument("--cap", type=int, default=28)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="circuit", choices=["circuit", "pair"],
-                    help="circuit: 6x6 amplitude workload; pair: one pairwise contraction (microbenchmark)")
+    ap.add_argument("--workload", default="circuit", choices=["circuit", "pair", "noisy"],
+                    help="circuit: 6x6 amplitude workload; pair: one pairwise contraction (microbenchmark); "
+                         "noisy: 4x5 noisy trajectory workload")
     ap.add_argument("--mnk", default="12,12,12", help="pair workload: log2 of M, N, K")
+    ap.add_argument("--path", default="best", choices=["best", "learned"],
+                    help="best: fewest sliced flops over the candidate trees; learned: least time predicted by "
+                         "the cost model in --model")
+    ap.add_argument("--model", default=os.path.join(ROOT, "paper_2104_10523_gb300", "data", "costmodel_tf32x3.npy"),
+                    help="trained cost-model parameters (float32 .npy, hidden 256) for --path learned")
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-min-slices", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--dump-amplitudes", default=None,
                     help="write the accuracy pass's amplitudes (every mode) to this JSON file")
+    ap.add_argument("--dump-timings", default=None,
+                    help="write the per-kernel records of the roofline pass (tnq_ctx_get_timings) to this JSON file")
     return ap.parse_args()
 
 
@@ -206,6 +218,8 @@ def main():
         return run_reference(a, world, rank)
     if a.workload == "pair":
         return run_pair(a, local, rank)
+    if a.workload == "noisy":
+        return run_noisy(a, local, rank)
 
     import numpy as np
     import torch
@@ -222,8 +236,21 @@ def main():
     bits_all = random_bitstrings(circ.n, WORKLOAD["n_bitstrings"], WORKLOAD["bits_seed"])
     B = 2 ** a.batch_log2
     t_plan = time.perf_counter()
-    plan = tnq.Plan(tnq.Circuit(circ), max_intermediate_log2=a.cap, batch_log2=a.batch_log2,
-                    path_mode=tnq.TNQ_PATH_BEST, n_candidates=a.candidates, seed=7)
+    path_info = {"path": a.path}
+    if a.path == "learned":
+        import numpy as np
+        mctx = tnq.Context(local, a.precision)
+        model = tnq.CostModel(mctx, hidden=256, max_batch=4096, seed=1)
+        model.set_params(np.load(a.model))
+        plan = model.plan(tnq.Circuit(circ), max_intermediate_log2=a.cap, batch_log2=a.batch_log2,
+                          path_mode=tnq.TNQ_PATH_BEST, n_candidates=a.candidates, seed=7)
+        cand = plan.candidates()
+        path_info.update({"chosen": int(cand["chosen"]), "flop_minimal": int(cand["flopmin"]),
+                          "flops_ratio_vs_flop_minimal": float(cand["flops"][cand["chosen"]] /
+                                                               cand["flops"][cand["flopmin"]])})
+    else:
+        plan = tnq.Plan(tnq.Circuit(circ), max_intermediate_log2=a.cap, batch_log2=a.batch_log2,
+                        path_mode=tnq.TNQ_PATH_BEST, n_candidates=a.candidates, seed=7)
     t_plan = time.perf_counter() - t_plan
     log(f"plan: {plan.info['n_steps']} steps, 2^{plan.info['n_sliced']} slices, "
         f"{plan.info['flops_per_batch']:.3e} flops/step, search {t_plan:.1f} s")
@@ -302,6 +329,10 @@ def main():
     rec = tnq.tnq_ctx_get_timings(ctx.h)
     tnq.tnq_ctx_set_timing(ctx.h, False)
     roofline, kernel_share = roofline_of(rec, a.precision)
+    if a.dump_timings and rank == 0:
+        with open(a.dump_timings, "w") as f:
+            json.dump({"fields": list(tnq.TIMING_FIELDS), "records": rec.tolist(),
+                       "steps": plan.steps().tolist()}, f)
 
     log("roofline pass done")
     # ---- accuracy against the FP64 oracle on the stored bitstrings (same plan, same
@@ -364,7 +395,8 @@ def main():
         "config": {"workload": workload_desc(a), "bitstrings_per_step": B, "slices": 2 ** info["n_sliced"],
                    "max_intermediate_log2": info["max_log2"], "flops_per_step": flops_step,
                    "path_search_s": round(t_plan, 2), "autotune_s": round(t_tune, 2),
-                   "autotuned_steps": {"tensor_core": n_tc, "cuda_core": n_cc}, "l2": "working set larger than L2 (intermediates up to "
+                   "autotuned_steps": {"tensor_core": n_tc, "cuda_core": n_cc}, "path": path_info,
+                   "l2": "working set larger than L2 (intermediates up to "
                    f"2^{info['max_log2']} x 8 B)", "parallelism": f"dp{world} (independent bitstrings)"},
         "contraction_tflops": tflops,
         "accuracy": accuracy,
@@ -510,6 +542,102 @@ def run_pair(a, local, rank):
             "config": {"workload": f"pairwise contraction M=2^{m} N=2^{n} K=2^{k}, complex64 all-dim-2 tensors"},
             "rel_l2_vs_fp64": err, "roofline": roofline, "kernel_share": share}
     if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_noisy(a, local, rank):
+    """Noisy workload: 4x5 grid random circuit, 10 cycles, depolarizing p = 1e-3
+    on every qubit after every gate and amplitude damping gamma = 1e-3 per cycle
+    (Kraus channels, Eq. kraus_sum); one step = the trajectory estimate of 256
+    bitstring probabilities from 4096 trajectories (FP64 averaging), i.e.
+    4096 x 256 trajectory amplitudes.  Checked against the exact probabilities
+    of the doubled density-matrix network (Sec. 3.3) on the same GPU."""
+    import numpy as np
+    import torch
+    from paper_2104_10523_gb300 import build, tnq
+    from workloads import CONFIG_NOISY as cfg, noisy_grid_circuit, random_bitstrings
+    torch.cuda.set_device(local)
+    build.build()
+    tnq.load()
+    circ = noisy_grid_circuit(cfg["rows"], cfg["cols"], cfg["cycles"], cfg["seed"], cfg["p_depol"], cfg["gamma"])
+    bits = random_bitstrings(circ.n, cfg["n_bitstrings"], cfg["bits_seed"])
+    n_traj, nb = cfg["n_trajectories"], len(bits)
+    plan = tnq.Plan(tnq.Circuit(circ), batch_log2=4, traj_log2=8, max_intermediate_log2=a.cap,
+                    path_mode=tnq.TNQ_PATH_BEST, n_candidates=256, seed=1)
+    ctx = tnq.Context(local, a.precision)
+    ctx.bind(plan)
+    tnq.tnq_plan_autotune(ctx.h, plan.h, 2)
+    dbits = torch.from_numpy(bits).cuda()
+    p_dev = torch.empty(nb, dtype=torch.float64, device="cuda")
+    se_dev = torch.empty(nb, dtype=torch.float64, device="cuda")
+
+    def step(seed):
+        tnq.tnq_noisy_probabilities(ctx.h, plan.h, n_traj, seed, dbits, p_dev, se_dev)
+
+    for i in range(a.warmup):
+        step(cfg["traj_seed"])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    n0 = tnq.tnq_ctx_launch_count(ctx.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for i in range(a.steps):
+        step(cfg["traj_seed"])
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    launches = tnq.tnq_ctx_launch_count(ctx.h) - n0
+    dt = e0.elapsed_time(e1) / 1e3 / a.steps
+    distinct = tnq.tnq_plan_get_info(plan.h)["distinct_trajectories"]
+    p_est, se = p_dev.cpu().numpy(), se_dev.cpu().numpy()
+    # end to end with host buffers
+    hb = torch.from_numpy(bits).pin_memory()
+    hp = torch.empty(nb, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        tnq.tnq_noisy_probabilities(ctx.h, plan.h, n_traj, cfg["traj_seed"], hb, hp, None)
+    torch.cuda.synchronize()
+    e2e_dt = (time.perf_counter() - t0) / a.steps
+    # exact probabilities from the doubled network, same bitstrings
+    dplan = tnq.Plan(tnq.Circuit(circ), density=True, batch_log2=0, max_intermediate_log2=27, n_candidates=256,
+                     seed=3)
+    dctx = tnq.Context(local, "fp32")
+    dctx.bind(dplan)
+    t_ex = time.perf_counter()
+    p_exact = dctx.density_probabilities(dplan, bits)
+    t_ex = time.perf_counter() - t_ex
+    z = np.abs(p_est - p_exact) / np.maximum(se, 1e-300)
+    unit = "trajectory amplitudes/s"
+    line = {"metric": "noisy bitstring probabilities by stochastic trajectories", "value": n_traj * nb / dt,
+            "unit": unit, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": a.precision,
+            "data": "synthetic",
+            "config": {"workload": "4x5 grid random circuit, 10 cycles, depolarizing p=1e-3 after every gate, "
+                       "amplitude damping gamma=1e-3 per cycle; 4096 trajectories x 256 bitstrings per step",
+                       "bitstrings_per_pass": 16, "trajectories_per_pass": 256,
+                       "distinct_trajectories": int(distinct), "slices": 2 ** plan.info["n_sliced"]},
+            "accuracy": {"exact": "doubled density-matrix network (tnq_density_probabilities, FP32)",
+                         "max_abs_z": float(z.max()), "mean_abs_z": float(z.mean()),
+                         "within_4_se": bool(np.all(np.abs(p_est - p_exact) <= 4 * se + 1e-6 * p_exact)),
+                         "exact_ms_per_bitstring": t_ex / nb * 1e3},
+            "e2e": {"value": n_traj * nb / e2e_dt, "unit": unit, "h2d_bytes_per_step": int(bits.size),
+                    "d2h_bytes_per_step": int(8 * nb)},
+            "gpu_launches": int(launches), "clocks": clocks.summary()}
+    if rank == 0:
+        # the oracle on the host cores: statevector trajectories (O1) for a bounded sample
+        from oracle import noise as onoise, statevector as osv
+        tc = time.perf_counter()
+        k = 0
+        while k < 2 or time.perf_counter() - tc < a.cpu_seconds:
+            onoise.noisy_probabilities(circ, bits, 1, cfg["traj_seed"] + k, osv.amplitudes)
+            k += 1
+        tc = time.perf_counter() - tc
+        line["cpu_baseline"] = {"value": k * nb / tc, "unit": unit, "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": f"oracle O1 (FP64 statevector per trajectory, all 256 bitstrings) for "
+                                          f"{k} trajectories in {tc:.1f} s"}
         print(json.dumps(line), flush=True)
 
 
