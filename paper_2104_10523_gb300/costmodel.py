@@ -122,6 +122,28 @@ def summarize(rows):
             "losses": int((r > 0.02).sum()), "same_pick": int(sum(x["same_pick"] for x in rows))}
 
 
+def run_config5(ctx, precision="tf32x3", max_flops=1e12, epochs=30, save=None):
+    """The cost-model workload: training circuits from seeds 0-1999 and held-out
+    circuits from seeds 2000-2199 whose flops stay within max_flops, one
+    executed plan per training circuit, 32 candidate trees per held-out
+    circuit.  Returns the summary (see main)."""
+    from workloads import cost_model_circuit
+    t0 = time.time()
+    train_c = pick_circuits(range(0, 2000), max_flops, cost_model_circuit, quick=True)
+    eval_c = pick_circuits(range(2000, 2200), max_flops, cost_model_circuit, quick=True)
+    t_pick = time.time() - t0
+    X, t = collect(ctx, train_c, 1, precision)
+    t_collect = time.time() - t0 - t_pick
+    model = tnq.CostModel(ctx, hidden=256, max_batch=4096, seed=1)
+    loss = model.train(X, t, epochs=epochs, batch=1024, lr=1e-3)
+    if save:
+        np.save(save, model.get_params())
+    rows = evaluate(ctx, model, eval_c, n_candidates=32)
+    return {"train_circuits": len(train_c), "eval_circuits": len(eval_c), "train_rows": int(len(t)),
+            "final_loss": loss, "target_variance": float(np.var(t)), "eval": summarize(rows),
+            "seconds": {"pick": t_pick, "collect": t_collect, "total": time.time() - t0}, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=64, help="training circuits (seeds 0..)")
@@ -140,9 +162,8 @@ def main():
     t0 = time.time()
     ctx = tnq.Context(0, a.precision)
     if a.config5:
-        train_c = pick_circuits(range(0, 2000), a.max_flops, cost_model_circuit, quick=True)
-        eval_c = pick_circuits(range(2000, 2200), a.max_flops, cost_model_circuit, quick=True)
-        a.candidates = 32
+        print(json.dumps(run_config5(ctx, a.precision, a.max_flops, a.epochs, a.save)))
+        return
     else:
         train_c = pick_circuits(range(0, 4 * a.train), a.max_flops, cost_model_circuit)[: a.train]
         eval_c = pick_circuits(range(2000, 2000 + 4 * a.eval), a.max_flops, cost_model_circuit)[: a.eval]

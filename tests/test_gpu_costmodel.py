@@ -130,3 +130,22 @@ def test_learned_ranking_vs_flop_ranking(T):
     assert s["n"] == len(eval_c)
     # the learned pick is not systematically slower than the FLOP-minimal one
     assert s["geomean_ratio"] <= 1.10, s
+
+
+def test_learned_ranking_gain_at_workload_scale(T):
+    """The cost-model workload at its own scale: the model is trained on step
+    timings of the training circuits (seeds 0-1999 up to 1e12 flops, about
+    1,500 circuits) and ranks 32 candidate trees of each held-out circuit
+    (seeds 2000-2199); the measured time of its pick is compared with the
+    FLOP-minimal pick's.  The learned ranking must gain: geometric-mean time
+    ratio below 0.95, and more wins than losses."""
+    from paper_2104_10523_gb300 import costmodel
+    ctx = T.Context(0, "tf32x3")
+    out = costmodel.run_config5(ctx, "tf32x3", 1e12, epochs=30)
+    s = out["eval"]
+    print("config-5 learned vs FLOP-minimal:", {k: out[k] for k in out if k != "rows"})
+    assert out["train_circuits"] >= 1000 and s["n"] >= 100
+    assert out["final_loss"] < 0.2 * out["target_variance"]
+    assert s["geomean_ratio"] < 0.95, s
+    assert s["wins"] > s["losses"], s
+
