@@ -178,7 +178,7 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
                          const std::vector<int>& a_req, const std::vector<int>& b_req,
                          const std::vector<int>& slice_labels, int slice_id, int nH, int nM, int nN, int nK,
                          char* scratch_a, char* scratch_b, void* C, void* acc, int* err, void* part,
-                         int choice = -1) {
+                         size_t scratch_a_bytes, int choice = -1) {
   // Small, skinny or K-degenerate steps run on the CUDA cores in FP32 whatever
   // the mode: they are launch- or bandwidth-bound and a tensor-core tile would
   // idle.  An autotuned choice (0 CUDA cores, 1 tensor cores) overrides the rule.
@@ -196,9 +196,15 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
   // split and multiplied on the tensor cores in one kernel (choice 2, and the
   // default where the shape qualifies).
   const int n_small = std::min(nM, nN), n_big = std::max(nM, nN);
+  // Long-K tall-skinny steps expand the small operand into scratch A (after
+  // the small operand itself when that one is permuted into scratch A)
+  const size_t tr_used = (nM <= nN && perm_a) ? ((8 * (size_t(1) << a_req.size()) + 4095) & ~size_t(4095)) : 0;
+  char* tr_scratch = scratch_a + tr_used;
+  const size_t tr_avail = scratch_a_bytes > tr_used ? scratch_a_bytes - tr_used : 0;
   const bool tc_rows_ok = choice != 0 && choice != 1 && ctx->precision != TNQ_PREC_FP32 && n_small <= 7 &&
                           !use_dot(nM, nN, nK) &&
-                          tc_rows_supported(1 << n_small, 1 << n_big, 1 << nK, 1 << nH, n_big + nH, ctx->precision);
+                          tc_rows_supported(1 << n_small, 1 << n_big, 1 << nK, 1 << nH, n_big + nH, ctx->precision) &&
+                          tc_rows_scratch_bytes(1 << n_small, 1 << nK, 1 << nH, ctx->precision) <= tr_avail;
   if (tc_rows_ok || (!use_tc && (rows_capable(nM, nN) || use_dot(nM, nN, nK)) && part)) {
     // bandwidth-bound skinny step: complex64 operands in [h][m|n][k] order
     // The large operand of a short-K rows step is read in place (fused gather)
@@ -274,9 +280,9 @@ tnq_status run_gemm_step(Ctx* ctx, const void* a_src, const std::vector<int>& a_
       cudaError_t e;
       if (tc_rows_ok)
         e = small_is_a ? launch_cgemm_tc_rows(Ssm, Gs, gd, C, acc, M, N, K, H, N, 1, slice_id, ctx->precision, err,
-                                              ctx->sm_count, ctx->stream)
+                                              ctx->sm_count, ctx->stream, tr_scratch, tr_avail)
                        : launch_cgemm_tc_rows(Ssm, Gs, gd, C, acc, N, M, K, H, 1, N, slice_id, ctx->precision, err,
-                                              ctx->sm_count, ctx->stream);
+                                              ctx->sm_count, ctx->stream, tr_scratch, tr_avail);
       else
         e = small_is_a ? launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, M, N, K, H, N, 1, slice_id, ctx->stream)
                        : launch_cgemm_rows_gather(Ssm, Gs, gd, C, acc, N, M, K, H, 1, N, slice_id, ctx->stream);
@@ -414,7 +420,7 @@ tnq_status run_step(Ctx* ctx, Plan* p, size_t si, int slice_id, char* ws, int ch
   return run_gemm_step(ctx, ws + ta.offset, ta.labels, s.perm_a, ws + tb.offset, tb.labels, s.perm_b, s.a_req,
                        s.b_req, sl, s.sliced_batch ? 0 : slice_id, s.nH, s.nM, s.nN, s.nK, ws + p->ws_scratch_a,
                        ws + p->ws_scratch_b, C, acc, reinterpret_cast<int*>(ws + p->ws_misc + 4),
-                       ws + p->ws_partial, choice);
+                       ws + p->ws_partial, p->ws_scratch_b - p->ws_scratch_a, choice);
 }
 
 // Kernel choice of a step under TNQ_KERNELS_TENSOR_CORES: the tall-skinny
@@ -1125,7 +1131,7 @@ tnq_status exec_contract_pair(Ctx* ctx, const void* A, int ra, const int* al, co
   std::vector<int> none;
   tnq_status st = run_gemm_step(ctx, pa, xa, xa != a_req, pb, xb, xb != b_req, a_req, b_req, none, 0,
                                 (int)Hh.size(), (int)M.size(), (int)N.size(), (int)K.size(), sa, sb,
-                                direct ? C : (void*)sc, nullptr, err, part);
+                                direct ? C : (void*)sc, nullptr, err, part, size_t(sb - sa));
   if (st != TNQ_OK) return st;
   if (!direct) {
     PermDesc d;

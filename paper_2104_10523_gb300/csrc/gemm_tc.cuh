@@ -36,14 +36,19 @@ struct GatherDesc;
 
 // Tall-skinny tensor-core GEMM (gemm_tc_rows.cu): out[h][s][g] (strides
 // s_stride_out, g_stride_out; batch stride ns * ng) = sum_k S[h][s][k] G[h][g][k]
-// for a small operand S ([batch][ns][K] complex64, ns <= 128, K <= 64 in BF16x3
-// or 32 in the TF32 modes) and a large one G read in
+// for a small operand S ([batch][ns][K] complex64, ns <= 128, K <= 256) and a
+// large one G read in
 // its stored bit order through gd, split into BF16 or TF32 hi/lo parts in
 // shared memory.  Adds into the FP64 acc when non-null, else writes C.
+// K up to 64 keeps S' whole in shared memory; K of 128 or 256 streams it per
+// K-part from a global copy built in `scratch` (tc_rows_scratch_bytes, 256-byte
+// aligned; cudaErrorNotSupported when it is missing or too small).
 bool tc_rows_supported(int ns, int ng, int K, int batch, int nrow, int precision);
+size_t tc_rows_scratch_bytes(int ns, int K, int batch, int precision);
 cudaError_t tc_rows_prepare();
 cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
                                  int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
-                                 int precision, int* err, int sm_count, cudaStream_t st);
+                                 int precision, int* err, int sm_count, cudaStream_t st, void* scratch = nullptr,
+                                 size_t scratch_bytes = 0);
 
 }  // namespace tnq

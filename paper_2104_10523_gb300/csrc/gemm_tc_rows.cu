@@ -24,10 +24,13 @@
 // expanded small operand of every batch entry does not fit in shared memory,
 // each batch entry gets its own launch.
 //
-// A tile's K range may be cut into K-parts of whole atoms: a shared-memory
-// stage then holds one part of a tile (the MMAs of a tile accumulate over its
-// parts), which lets TF32 rows of K = 64 (four atoms per part) run beside a
-// 128 KB expanded small operand.
+// A tile's K range may be cut into one-atom K-parts: a shared-memory stage
+// then holds one part of a tile (the MMAs of a tile accumulate over its
+// parts), which lets TF32 rows of K = 64 (four atoms) run in two stages
+// beside a 128 KB expanded small operand.  Rows of K = 128 or 256 stream the
+// expanded small operand as well: it is built once in global memory (where it
+// stays in L2) and each stage receives the K-part of it that its MMAs read, by
+// a bulk copy that completes on the stage's barrier.
 //
 // In the TF32 split mode the product hi*hi accumulates into one TMEM buffer
 // and the two correction products hi*lo, lo*hi into a second one; the
@@ -82,7 +85,7 @@ constexpr int TR_ROW_BYTES = 128;              // one swizzle atom of a row
 constexpr int TR_ATOM_BYTES = 128 * TR_ROW_BYTES;  // one atom column of a 128-row tile
 constexpr int TR_BPRIME_BUDGET = 128 * 1024;
 constexpr int TR_SMEM_LIMIT = 225 * 1024;      // dynamic shared memory of one CTA
-constexpr int TR_KMAX = 64;
+constexpr int TR_KMAX = 256;                  // longest K (in resident mode: 64)
 
 struct TrParams {
   const float2* S;        // small operand [batch][ns][K]
@@ -101,6 +104,9 @@ struct TrParams {
   int dual;               // 1: correction products in a second TMEM buffer
   int acc_cols;           // TMEM columns per accumulator buffer: npad, or 2 npad when dual
   int nchunks;            // converter chunks per part
+  int stream_bp;          // 1: S' streamed per K-part from bp_glob into each stage (long K)
+  const uint8_t* bp_glob; // streamed mode: S' expanded in global memory, same layout as in shared memory
+  uint32_t bp_part;       // streamed mode: bytes of one piece (hi or lo) of S' for one K-part
   int kind_bf16;          // 1: BF16 parts, kind::f16; 0: TF32 parts, kind::tf32
   int split;              // 1: three products (hi/lo); 0: one TF32 product
   int pairs;              // the lowest stored bit of G is K bit 0: 16-byte loads
@@ -217,6 +223,12 @@ __device__ void build_bprime(const TrParams& P, uint8_t* bp, int tid, int nthrea
   }
 }
 
+// S' of every batch entry expanded into global memory (streamed mode), in the
+// layout build_bprime gives it in shared memory.
+__global__ void build_bprime_kernel(const __grid_constant__ TrParams P, uint8_t* dst) {
+  build_bprime(P, dst, int(blockIdx.x * blockDim.x + threadIdx.x), int(gridDim.x * blockDim.x));
+}
+
 __device__ __forceinline__ size_t deposit(long long v, const int* pos, int n) {
   size_t o = 0;
   for (int j = 0; j < n; ++j)
@@ -255,7 +267,9 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
   __shared__ uint32_t koff[TR_KMAX];
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t stage_bytes = 2u * TR_ATOM_BYTES * uint32_t(P.patoms);  // hi + lo of one K-part
+  // a stage: G hi and lo of one K-part, then (streamed mode) S' hi and lo of that part
+  const uint32_t g_piece = TR_ATOM_BYTES * uint32_t(P.patoms);
+  const uint32_t stage_bytes = 2u * g_piece + (P.stream_bp ? 2u * P.bp_part : 0u);
   uint8_t* bprime = smem + size_t(P.stages) * stage_bytes;
   const uint32_t bp_atom = uint32_t(P.npad) * TR_ROW_BYTES;
   const uint32_t bp_half = bp_atom * uint32_t(P.atoms);
@@ -264,7 +278,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), 128);  // one converter group
+      // one converter group, plus the transaction arrival of the S' copy
+      mbar_init(smem_u32(&full_bar[s]), 128 + (P.stream_bp ? 1 : 0));
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int b = 0; b < P.nacc; ++b) {
@@ -280,7 +295,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       if ((kk >> j) & 1) o |= 1u << P.gd.kpos[j];
     koff[kk] = o;
   }
-  if (warp < TR_CONV_WARPS) build_bprime(P, bprime, threadIdx.x, 32 * TR_CONV_WARPS);
+  if (warp < TR_CONV_WARPS && !P.stream_bp) build_bprime(P, bprime, threadIdx.x, 32 * TR_CONV_WARPS);
   if (warp == TR_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(tmem_cols)
@@ -347,7 +362,17 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
         break;
       }
       uint8_t* st = smem + size_t(s) * stage_bytes;
-      store_chunk<CH>(st, st + stage_bytes / 2, r, buf[0], c, units, P.kind_bf16, P.split);
+      if (c == 0 && P.stream_bp && r == 0) {
+        // S' hi and lo of this item's K-part, copied into the stage by the bulk
+        // copy engine; the stage completes when both copies have landed
+        const uint32_t tt = item_tile(jc), kp = jc % uint32_t(kparts);
+        const uint8_t* src = P.bp_glob + size_t(tt / tph) * 2 * P.atoms * P.npad * TR_ROW_BYTES + size_t(kp) * P.bp_part;
+        const uint32_t bar = smem_u32(&full_bar[s]);
+        mbar_expect_tx(bar, 2u * P.bp_part);
+        bulk_g2s(smem_u32(st + 2 * g_piece), src, P.bp_part, bar);
+        bulk_g2s(smem_u32(st + 2 * g_piece + P.bp_part), src + size_t(P.atoms) * P.npad * TR_ROW_BYTES, P.bp_part, bar);
+      }
+      store_chunk<CH>(st, st + g_piece, r, buf[0], c, units, P.kind_bf16, P.split);
       if (c == nch - 1) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&full_bar[s]));
@@ -379,7 +404,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
           break;
         }
         const uint32_t h = t / tph;
-        const uint32_t b_hi = smem_u32(bprime) + h * 2 * bp_half, b_lo = b_hi + bp_half;
         const uint32_t d = tmem + uint32_t(b * P.acc_cols);
         const uint32_t dc = P.dual ? d + uint32_t(P.npad) : d;  // correction products
         for (int kp = 0; kp < kparts; ++kp) {
@@ -389,11 +413,15 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a_hi = smem_u32(smem + size_t(s) * stage_bytes), a_lo = a_hi + stage_bytes / 2;
+          const uint32_t a_hi = smem_u32(smem + size_t(s) * stage_bytes), a_lo = a_hi + g_piece;
+          // S': this part in the stage (streamed) or the whole row resident
+          const uint32_t b_hi = P.stream_bp ? a_hi + 2 * g_piece : smem_u32(bprime) + h * 2 * bp_half;
+          const uint32_t b_lo = b_hi + (P.stream_bp ? P.bp_part : bp_half);
           for (int kk = 0; kk < P.nks_part; ++kk) {
             const int kg = kp * P.nks_part + kk;  // K step within the row
             const uint32_t ao = uint32_t(kk >> 2) * TR_ATOM_BYTES + uint32_t(kk & 3) * 32;
-            const uint32_t bo = uint32_t(kg >> 2) * bp_atom + uint32_t(kg & 3) * 32;
+            const int kb = P.stream_bp ? kk : kg;  // K step within the S' buffer the MMA reads
+            const uint32_t bo = uint32_t(kb >> 2) * bp_atom + uint32_t(kb & 3) * 32;
             const uint32_t acc_on = kg > 0 ? 1u : 0u;
             if (P.split) {
               mma_issue(P.kind_bf16, dc, smem_desc(a_lo + ao), smem_desc(b_hi + bo), P.idesc, acc_on);
@@ -509,6 +537,7 @@ size_t tr_bprime_bytes(int ns, int K, int batch, bool bf16) {
 // the expanded small operand (bprime bytes) must fit the shared-memory limit.
 struct TrStages {
   int kparts = 0, patoms = 0, stages = 0;
+  bool stream = false;  // S' streamed per K-part (K > 64)
 };
 
 TrStages tr_stages(int atoms, size_t bprime) {
@@ -528,9 +557,29 @@ TrStages tr_stages(int atoms, size_t bprime) {
   return t;
 }
 
+// Streamed layout (K > 64): one-atom K-parts; a stage holds G hi and lo and
+// the same part of S' hi and lo (npad rows of one atom each).
+TrStages tr_stages_streamed(int atoms, int npad) {
+  TrStages t;
+  t.kparts = atoms;
+  t.patoms = 1;
+  t.stream = true;
+  const size_t stage_bytes = size_t(2) * TR_ATOM_BYTES + size_t(2) * npad * TR_ROW_BYTES;
+  t.stages = 4;
+  while (t.stages > 2 && size_t(t.stages) * stage_bytes + 1024 > size_t(TR_SMEM_LIMIT)) t.stages -= 2;
+  if (size_t(t.stages) * stage_bytes + 1024 > size_t(TR_SMEM_LIMIT)) t.stages = 0;
+  return t;
+}
+
 constexpr size_t TR_SMEM_MAX = size_t(TR_SMEM_LIMIT);
+constexpr int TR_RESIDENT_KMAX = 64;
 
 }  // namespace
+
+size_t tc_rows_scratch_bytes(int ns, int K, int batch, int precision) {
+  if (K <= TR_RESIDENT_KMAX) return 0;
+  return tr_bprime_bytes(ns, K, batch, precision == TNQ_PREC_BF16X3);
+}
 
 cudaError_t tc_rows_prepare() {
   static cudaError_t result = cudaErrorUnknown;
@@ -547,8 +596,10 @@ cudaError_t tc_rows_prepare() {
 bool tc_rows_supported(int ns, int ng, int K, int batch, int nrow, int precision) {
   if (precision != TNQ_PREC_TF32 && precision != TNQ_PREC_TF32X3 && precision != TNQ_PREC_BF16X3) return false;
   const bool bf16 = precision == TNQ_PREC_BF16X3;
-  // rows of 2K reals span at most four swizzle atoms; MMA N = 2 ns <= 256
+  // MMA N = 2 ns <= 256; K up to 256 (rows of more than 64 complex values
+  // stream S' through the stages)
   if (ns < 1 || ns > 128 || K < 1 || K > TR_KMAX || ng < 128 || (ng & 127) || batch < 1 || nrow < 7) return false;
+  if (K > TR_RESIDENT_KMAX) return K >= 128 && tr_stages_streamed(tr_atoms(K, bf16), tr_npad(ns)).stages >= 2;
   // S' of one batch entry must fit beside at least two stages (larger batches
   // run one launch per entry)
   const size_t bp = tr_bprime_bytes(ns, K, 1, bf16);
@@ -559,7 +610,8 @@ namespace {
 
 cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
                                int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
-                               int precision, int* err, int sm_count, cudaStream_t st) {
+                               int precision, int* err, int sm_count, cudaStream_t st, void* scratch = nullptr,
+                               size_t scratch_bytes = 0) {
   TrParams P;
   P.S = reinterpret_cast<const float2*>(Ssmall);
   P.G = reinterpret_cast<const float2*>(Gsrc);
@@ -574,8 +626,14 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   const int k_step = P.kind_bf16 ? 8 : 4;  // complex values per 32-byte MMA K step
   P.nks = (K + k_step - 1) / k_step;
   P.atoms = tr_atoms(K, P.kind_bf16 != 0);
-  const TrStages ts = tr_stages(P.atoms, tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0));
+  const size_t bp_all = tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0);
+  const TrStages ts = K > TR_RESIDENT_KMAX ? tr_stages_streamed(P.atoms, P.npad) : tr_stages(P.atoms, bp_all);
   if (ts.stages < 2) return cudaErrorNotSupported;
+  P.stream_bp = ts.stream ? 1 : 0;
+  P.bp_part = uint32_t(ts.patoms) * uint32_t(P.npad) * TR_ROW_BYTES;
+  P.bp_glob = reinterpret_cast<const uint8_t*>(scratch);
+  if (P.stream_bp && (!scratch || scratch_bytes < bp_all || (reinterpret_cast<uintptr_t>(scratch) & 255)))
+    return cudaErrorNotSupported;
   P.kparts = ts.kparts;
   P.patoms = ts.patoms;
   P.stages = ts.stages;
@@ -603,8 +661,14 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   P.acc = reinterpret_cast<double2*>(acc);
   P.err = err;
   const long long grid = std::min<long long>(P.total_tiles, std::max(1, sm_count));
-  const size_t smem = size_t(P.stages) * 2 * P.patoms * TR_ATOM_BYTES +
-                      tr_bprime_bytes(ns, K, batch, P.kind_bf16 != 0) + 1024;
+  const size_t smem = size_t(P.stages) * (2 * P.patoms * TR_ATOM_BYTES + (P.stream_bp ? 2 * size_t(P.bp_part) : 0)) +
+                      (P.stream_bp ? 0 : bp_all) + 1024;
+  if (P.stream_bp) {
+    // S' of every batch entry, expanded once into the scratch for this launch
+    const long long n = (long long)batch * P.npad * P.nks * (32 / (P.kind_bf16 ? 2 : 4));
+    const unsigned blocks = unsigned(std::min<long long>((n + 255) / 256, 1024));
+    build_bprime_kernel<<<blocks, 256, 0, st>>>(P, reinterpret_cast<uint8_t*>(scratch));
+  }
   if (ch == 8)
     cgemm_tc_rows_kernel<8, 4><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   else
@@ -616,12 +680,16 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
 
 cudaError_t launch_cgemm_tc_rows(const void* Ssmall, const void* Gsrc, const GatherDesc& gd, void* C, void* acc, int ns,
                                  int ng, int K, int batch, long long s_stride_out, long long g_stride_out, int slice_id,
-                                 int precision, int* err, int sm_count, cudaStream_t st) {
+                                 int precision, int* err, int sm_count, cudaStream_t st, void* scratch,
+                                 size_t scratch_bytes) {
   if (!tc_rows_supported(ns, ng, K, batch, gd.nrow, precision) || !err) return cudaErrorNotSupported;
-  if (gd.nk > 6 || gd.nrow > 32 || (1 << gd.nk) != K) return cudaErrorInvalidValue;
+  if (gd.nk > 8 || gd.nrow > 32 || (1 << gd.nk) != K) return cudaErrorInvalidValue;
   cudaError_t pe = tc_rows_prepare();
   if (pe != cudaSuccess) return pe;
   const bool bf16 = precision == TNQ_PREC_BF16X3;
+  if (K > TR_RESIDENT_KMAX)
+    return launch_tc_rows_one(Ssmall, Gsrc, gd, C, acc, ns, ng, K, batch, s_stride_out, g_stride_out, slice_id,
+                              precision, err, sm_count, st, scratch, scratch_bytes);
   const size_t bp_all = tr_bprime_bytes(ns, K, batch, bf16);
   if (bp_all <= size_t(TR_BPRIME_BUDGET) && tr_stages(tr_atoms(K, bf16), bp_all).stages >= 2)
     return launch_tc_rows_one(Ssmall, Gsrc, gd, C, acc, ns, ng, K, batch, s_stride_out, g_stride_out, slice_id,

@@ -51,6 +51,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Bulk copy (no tensor map) of `bytes` bytes, a multiple of 16, from global to
+// shared memory; both addresses 16-byte aligned.  Completes `bytes`
+// transactions on the mbarrier at `mbar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand in 128B-swizzled rows,
 // 8-row core groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {

@@ -142,13 +142,15 @@ def test_invalid_labels_rejected(T):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16x3"])
-@pytest.mark.parametrize("shape", [(6, 16, 6), (5, 16, 6), (6, 15, 5), (4, 17, 6), (6, 14, 3)])
+@pytest.mark.parametrize("shape", [(6, 16, 6), (5, 16, 6), (6, 15, 5), (4, 17, 6), (6, 14, 3),
+                                   (6, 14, 8), (4, 15, 7), (2, 16, 8)])
 def test_tall_skinny_long_k(T, prec, shape):
     """Tall-skinny steps of the benchmark's shape class (2^s <= 64 small rows,
     2^g large rows, K = 2^k up to 64, operand bits scattered) run on the
     tall-skinny tcgen05 kernel (timing kind 5) in every tensor-core mode; in
     TF32 with K = 64 a 128-row tile passes through shared memory in four
-    K-parts.  The split modes keep the correction products in their own TMEM
+    K-parts; with K = 128 or 256 the expanded small operand is streamed from a
+    global copy into each stage beside its K-part.  TF32x3 keeps the correction products in their own TMEM
     accumulator, so TF32x3 stays within a few FP32 roundings of the FP64
     result."""
     import torch
