@@ -26,7 +26,7 @@
 //
 // A tile's K range may be cut into one-atom K-parts: a shared-memory stage
 // then holds one part of a tile (the MMAs of a tile accumulate over its
-// parts), which lets TF32 rows of K = 64 (four atoms) run in two stages
+// parts), which lets TF32 rows of K = 64 (four atoms) run in three stages
 // beside a 128 KB expanded small operand.  Rows of K = 128 or 256 stream the
 // expanded small operand as well: it is built once in global memory (where it
 // stays in L2) and each stage receives the K-part of it that its MMAs read, by
@@ -79,7 +79,7 @@ using namespace tcx;
 constexpr int TR_CONV_WARPS = 8;
 constexpr int TR_THREADS = 32 * (TR_CONV_WARPS + 1 + 4);
 constexpr int TR_MMA_WARP = TR_CONV_WARPS;
-constexpr int TR_MAX_STAGES = 4;               // even: stage parity = converter group
+constexpr int TR_MAX_STAGES = 4;
 constexpr int TR_MAX_NACC = 4;                 // TMEM accumulator buffers
 constexpr int TR_ROW_BYTES = 128;              // one swizzle atom of a row
 constexpr int TR_ATOM_BYTES = 128 * TR_ROW_BYTES;  // one atom column of a 128-row tile
@@ -99,7 +99,7 @@ struct TrParams {
   int patoms;             // atoms per part: atoms / kparts
   int nks_part;           // MMA K steps per part
   int kc;                 // complex values per part
-  int stages;             // shared-memory stages, each holding one part (even)
+  int stages;             // shared-memory stages, each holding one part
   int nacc;               // TMEM accumulator buffers
   int dual;               // 1: correction products in a second TMEM buffer
   int acc_cols;           // TMEM columns per accumulator buffer: npad, or 2 npad when dual
@@ -352,9 +352,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       advance_load();
     }
     uint32_t jc = uint32_t(grp);  // convert cursor
-    int s = grp, c = 0;
-    uint32_t ph = 0;
+    int c = 0;
     while (item_tile(jc) < total) {
+      // item jc uses stage jc % stages in phase (jc / stages) & 1; its empty
+      // wait orders it after the MMAs of item jc - stages, whichever group
+      // converted that one, so any stage count works
+      const int s = int(jc % uint32_t(P.stages));
+      const uint32_t ph = (jc / uint32_t(P.stages)) & 1u;
       if (tl < total) load_chunk<CH>(P, koff, bl, int(jl % uint32_t(kparts)), cl, buf[DEPTH]);
       advance_load();
       if (c == 0 && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
@@ -376,11 +380,6 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       if (c == nch - 1) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&full_bar[s]));
-        s += 2;  // this group's next item
-        if (s >= P.stages) {
-          s -= P.stages;
-          ph ^= 1;
-        }
       }
 #pragma unroll
       for (int d = 0; d < DEPTH; ++d)
@@ -552,7 +551,9 @@ TrStages tr_stages(int atoms, size_t bprime) {
     t.stages = 4;
   }
   const size_t stage_bytes = size_t(2) * TR_ATOM_BYTES * t.patoms;
-  while (t.stages > 2 && size_t(t.stages) * stage_bytes + bprime + 1024 > size_t(TR_SMEM_LIMIT)) t.stages -= 2;
+  // one-atom parts may take an odd number of stages (three beside a 128 KB S')
+  const int step = t.kparts > 1 ? 1 : 2;
+  while (t.stages > 2 && size_t(t.stages) * stage_bytes + bprime + 1024 > size_t(TR_SMEM_LIMIT)) t.stages -= step;
   if (size_t(t.stages) * stage_bytes + bprime + 1024 > size_t(TR_SMEM_LIMIT)) t.stages = 0;
   return t;
 }
@@ -566,7 +567,7 @@ TrStages tr_stages_streamed(int atoms, int npad) {
   t.stream = true;
   const size_t stage_bytes = size_t(2) * TR_ATOM_BYTES + size_t(2) * npad * TR_ROW_BYTES;
   t.stages = 4;
-  while (t.stages > 2 && size_t(t.stages) * stage_bytes + 1024 > size_t(TR_SMEM_LIMIT)) t.stages -= 2;
+  while (t.stages > 2 && size_t(t.stages) * stage_bytes + 1024 > size_t(TR_SMEM_LIMIT)) t.stages -= 1;
   if (size_t(t.stages) * stage_bytes + 1024 > size_t(TR_SMEM_LIMIT)) t.stages = 0;
   return t;
 }
