@@ -18,9 +18,11 @@
 // tensor), split into hi/lo parts (BF16 or TF32) by converter warps and written
 // straight into the 128-byte-swizzled K-major layout the MMA reads (128-byte
 // swizzle atoms of K per row).  The output is written once.  Per 128-row
-// tile: 128 * K * 8 bytes in, 128 * ns * 8 bytes out, 3 * ceil(2K / k_step)
-// MMAs of 128 x Npad (Npad = max(16, 2 ns) <= 256; four TMEM accumulator
-// buffers for Npad <= 64, two above, at most all 512 columns).  When the
+// tile: 128 * K * 8 bytes in, 128 * ns * 8 bytes out, 2 * ceil(2K / k_step)
+// MMAs in the split modes (Npad = max(16, 2 ns) <= 128: one of 128 x 2 Npad
+// over S' hi and lo rows side by side, one of 128 x Npad; three of 128 x Npad
+// for Npad = 256), ceil(2K / k_step) in plain TF32; four TMEM accumulator
+// buffers for Npad <= 64, two above, at most all 512 columns.  When the
 // expanded small operand of every batch entry does not fit in shared memory,
 // each batch entry gets its own launch.
 //
@@ -32,9 +34,9 @@
 // stays in L2) and each stage receives the K-part of it that its MMAs read, by
 // a bulk copy that completes on the stage's barrier.
 //
-// In the TF32 split mode the product hi*hi accumulates into one TMEM buffer
-// and the two correction products hi*lo, lo*hi into a second one; the
-// epilogue adds them in FP32 registers.  The tensor-memory accumulator adds each MMA's
+// In the split modes the product hi*hi accumulates into one TMEM buffer
+// and the two correction products hi*lo, lo*hi into a second one beside it
+// (hi*hi and hi*lo are one MMA); the epilogue adds them in FP32 registers.  The tensor-memory accumulator adds each MMA's
 // result with truncation toward zero, so a chain of additions into the large
 // accumulator shrinks it by about half an ulp per addition; keeping the
 // corrections (about 2^-9 of it) apart cuts that chain to one addition per K
@@ -102,11 +104,12 @@ struct TrParams {
   int stages;             // shared-memory stages, each holding one part
   int nacc;               // TMEM accumulator buffers
   int dual;               // 1: correction products in a second TMEM buffer
+  int merged;             // 1 (dual): hi*hi and hi*lo in one MMA of N = 2 npad over S' hi and lo rows
   int acc_cols;           // TMEM columns per accumulator buffer: npad, or 2 npad when dual
   int nchunks;            // converter chunks per part
   int stream_bp;          // 1: S' streamed per K-part from bp_glob into each stage (long K)
   const uint8_t* bp_glob; // streamed mode: S' expanded in global memory, same layout as in shared memory
-  uint32_t bp_part;       // streamed mode: bytes of one piece (hi or lo) of S' for one K-part
+  uint32_t bp_part;       // streamed mode: bytes of S' hi (or lo) rows for one K-part
   int kind_bf16;          // 1: BF16 parts, kind::f16; 0: TF32 parts, kind::tf32
   int split;              // 1: three products (hi/lo); 0: one TF32 product
   int pairs;              // the lowest stored bit of G is K bit 0: 16-byte loads
@@ -114,7 +117,8 @@ struct TrParams {
   int tiles_per_h;        // ng / 128
   long long total_tiles;
   int slice_id;
-  uint32_t idesc;
+  uint32_t idesc;         // MMA of N = npad
+  uint32_t idesc2;        // MMA of N = 2 npad (merged)
   float2* C;
   double2* acc;
   int* err;
@@ -197,8 +201,9 @@ __device__ void build_bprime(const TrParams& P, uint8_t* bp, int tid, int nthrea
   const int es = P.kind_bf16 ? 2 : 4;
   const int reals = P.nks * (32 / es);
   const int per_h = P.npad * reals;
-  const uint32_t atom_bytes = uint32_t(P.npad) * TR_ROW_BYTES;
-  const uint32_t half_bytes = atom_bytes * P.atoms;
+  // per batch entry and atom column: npad hi rows, then npad lo rows
+  const uint32_t atom_bytes = 2u * uint32_t(P.npad) * TR_ROW_BYTES;
+  const uint32_t entry_bytes = atom_bytes * P.atoms;
   for (int e = tid; e < P.batch * per_h; e += nthreads) {
     const int h = e / per_h, rem = e % per_h, n = rem / reals, q = rem % reals;
     const int s = n >> 1, k = q >> 1;
@@ -208,8 +213,8 @@ __device__ void build_bprime(const TrParams& P, uint8_t* bp, int tid, int nthrea
       // row (s, re): [sr, -si] per k; row (s, im): [si, sr]
       x = (n & 1) ? ((q & 1) ? a.x : a.y) : ((q & 1) ? -a.y : a.x);
     }
-    uint8_t* hi = bp + size_t(h) * 2 * half_bytes;
-    uint8_t* lo = hi + half_bytes;
+    uint8_t* hi = bp + size_t(h) * entry_bytes;
+    uint8_t* lo = hi + uint32_t(P.npad) * TR_ROW_BYTES;  // row npad + n: same swizzle phase (npad % 16 == 0)
     const uint32_t off = swz(n, (q * es) >> 4, atom_bytes) + uint32_t((q * es) & 15);
     if (P.kind_bf16) {
       const uint32_t hb = bf16_bits(x);
@@ -271,8 +276,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
   const uint32_t g_piece = TR_ATOM_BYTES * uint32_t(P.patoms);
   const uint32_t stage_bytes = 2u * g_piece + (P.stream_bp ? 2u * P.bp_part : 0u);
   uint8_t* bprime = smem + size_t(P.stages) * stage_bytes;
-  const uint32_t bp_atom = uint32_t(P.npad) * TR_ROW_BYTES;
-  const uint32_t bp_half = bp_atom * uint32_t(P.atoms);
+  const uint32_t bp_atom = 2u * uint32_t(P.npad) * TR_ROW_BYTES;  // S' hi and lo rows of one atom column
+  const uint32_t bp_entry = bp_atom * uint32_t(P.atoms);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tmem_cols = uint32_t(P.acc_cols * P.nacc) < 32u ? 32u : uint32_t(P.acc_cols * P.nacc);
 
@@ -370,11 +375,10 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
         // S' hi and lo of this item's K-part, copied into the stage by the bulk
         // copy engine; the stage completes when both copies have landed
         const uint32_t tt = item_tile(jc), kp = jc % uint32_t(kparts);
-        const uint8_t* src = P.bp_glob + size_t(tt / tph) * 2 * P.atoms * P.npad * TR_ROW_BYTES + size_t(kp) * P.bp_part;
+        const uint8_t* src = P.bp_glob + size_t(tt / tph) * bp_entry + size_t(kp) * 2u * P.bp_part;
         const uint32_t bar = smem_u32(&full_bar[s]);
         mbar_expect_tx(bar, 2u * P.bp_part);
-        bulk_g2s(smem_u32(st + 2 * g_piece), src, P.bp_part, bar);
-        bulk_g2s(smem_u32(st + 2 * g_piece + P.bp_part), src + size_t(P.atoms) * P.npad * TR_ROW_BYTES, P.bp_part, bar);
+        bulk_g2s(smem_u32(st + 2 * g_piece), src, 2u * P.bp_part, bar);
       }
       store_chunk<CH>(st, st + g_piece, r, buf[0], c, units, P.kind_bf16, P.split);
       if (c == nch - 1) {
@@ -414,20 +418,27 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a_hi = smem_u32(smem + size_t(s) * stage_bytes), a_lo = a_hi + g_piece;
           // S': this part in the stage (streamed) or the whole row resident
-          const uint32_t b_hi = P.stream_bp ? a_hi + 2 * g_piece : smem_u32(bprime) + h * 2 * bp_half;
-          const uint32_t b_lo = b_hi + (P.stream_bp ? P.bp_part : bp_half);
+          const uint32_t b_hi = P.stream_bp ? a_hi + 2 * g_piece : smem_u32(bprime) + h * bp_entry;
+          // shared-memory addresses stay below 2^18, so a descriptor's address
+          // field (address >> 4) takes byte offsets >> 4 without carrying out
+          const uint64_t da_hi = smem_desc(a_hi), da_lo = smem_desc(a_lo), db_hi = smem_desc(b_hi);
+          const uint64_t db_lo = db_hi + uint64_t((uint32_t(P.npad) * TR_ROW_BYTES) >> 4);
           for (int kk = 0; kk < P.nks_part; ++kk) {
             const int kg = kp * P.nks_part + kk;  // K step within the row
-            const uint32_t ao = uint32_t(kk >> 2) * TR_ATOM_BYTES + uint32_t(kk & 3) * 32;
+            const uint64_t ao = uint64_t((uint32_t(kk >> 2) * TR_ATOM_BYTES + uint32_t(kk & 3) * 32) >> 4);
             const int kb = P.stream_bp ? kk : kg;  // K step within the S' buffer the MMA reads
-            const uint32_t bo = uint32_t(kb >> 2) * bp_atom + uint32_t(kb & 3) * 32;
+            const uint64_t bo = uint64_t((uint32_t(kb >> 2) * bp_atom + uint32_t(kb & 3) * 32) >> 4);
             const uint32_t acc_on = kg > 0 ? 1u : 0u;
-            if (P.split) {
-              mma_issue(P.kind_bf16, dc, smem_desc(a_lo + ao), smem_desc(b_hi + bo), P.idesc, acc_on);
-              mma_issue(P.kind_bf16, dc, smem_desc(a_hi + ao), smem_desc(b_lo + bo), P.idesc, 1u);
-              mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, P.dual ? acc_on : 1u);
+            if (P.merged) {
+              // columns [0, npad): hi*hi; [npad, 2 npad): hi*lo, then lo*hi added
+              mma_issue(P.kind_bf16, d, da_hi + ao, db_hi + bo, P.idesc2, acc_on);
+              mma_issue(P.kind_bf16, dc, da_lo + ao, db_hi + bo, P.idesc, 1u);
+            } else if (P.split) {
+              mma_issue(P.kind_bf16, dc, da_lo + ao, db_hi + bo, P.idesc, acc_on);
+              mma_issue(P.kind_bf16, dc, da_hi + ao, db_lo + bo, P.idesc, 1u);
+              mma_issue(P.kind_bf16, d, da_hi + ao, db_hi + bo, P.idesc, P.dual ? acc_on : 1u);
             } else {
-              mma_issue(P.kind_bf16, d, smem_desc(a_hi + ao), smem_desc(b_hi + bo), P.idesc, acc_on);
+              mma_issue(P.kind_bf16, d, da_hi + ao, db_hi + bo, P.idesc, acc_on);
             }
           }
           mma_commit(smem_u32(&empty_bar[s]));
@@ -641,10 +652,15 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   P.nks_part = P.kparts == 1 ? P.nks : 4 * P.patoms;  // parts of several atoms hold whole atoms of K
   P.kc = P.kparts == 1 ? K : P.patoms * TR_ROW_BYTES / (2 * (P.kind_bf16 ? 2 : 4));
   P.nacc = P.npad <= 64 ? 4 : 2;  // TMEM: acc_cols * nacc <= 512 columns
-  // TF32x3 sums are FP32-accurate except for the truncating accumulation, so
-  // they take the separate correction buffer; BF16x3 errors are dominated by
-  // its 16-bit operand split, where the extra TMEM reads buy nothing
-  P.dual = (P.split && !P.kind_bf16 && P.npad <= 128) ? 1 : 0;
+  // The split modes keep the correction products in a second TMEM buffer
+  // beside the hi*hi one, so that hi*hi and hi*lo come from one MMA of
+  // N = 2 npad over S' hi and lo rows (two MMAs per K step instead of three;
+  // each MMA instruction has a fixed issue cost of the order of 10^2 cycles,
+  // which dominates these short-K tiles) and the TF32 sums escape most of the
+  // truncating accumulation (the corrections, about 2^-9 of the sum, are added
+  // once in the epilogue).  N = 2 npad <= 256 bounds it to npad <= 128.
+  P.dual = (P.split && P.npad <= 128) ? 1 : 0;
+  P.merged = P.dual;
   P.acc_cols = P.npad * (P.dual ? 2 : 1);
   const int ch = P.kc <= 8 ? 8 : 16;
   P.nchunks = (P.kc + ch - 1) / ch;
@@ -658,6 +674,7 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   // instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1), K-major, N >> 3, M >> 4
   const uint32_t fmt = P.kind_bf16 ? 1u : 2u;
   P.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(P.npad >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+  P.idesc2 = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t((2 * P.npad) >> 3) << 17) | (uint32_t(128 >> 4) << 24);
   P.C = reinterpret_cast<float2*>(C);
   P.acc = reinterpret_cast<double2*>(acc);
   P.err = err;
