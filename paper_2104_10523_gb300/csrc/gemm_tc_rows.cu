@@ -260,9 +260,14 @@ __device__ __forceinline__ void load_chunk(const TrParams& P, const uint32_t* ko
   }
 }
 
-template <int CH, int DEPTH>
+// MODE: 0 plain TF32, 1 TF32x3, 2 BF16x3.  The converter loop is unrolled,
+// and a kernel holding every mode's conversion code made the rarely running
+// MMA warp miss in the instruction cache (about 200 cycles per group of
+// instructions it issued), so each mode is its own kernel.
+template <int CH, int DEPTH, int MODE>
 __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __grid_constant__ TrParams P) {
   extern __shared__ uint8_t smem_raw[];
+  constexpr int kBF16 = MODE == 2 ? 1 : 0, kSplit = MODE != 0 ? 1 : 0;
   __shared__ __align__(8) uint64_t full_bar[TR_MAX_STAGES];
   __shared__ __align__(8) uint64_t empty_bar[TR_MAX_STAGES];
   __shared__ __align__(8) uint64_t acc_full[TR_MAX_NACC];
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
         mbar_expect_tx(bar, 2u * P.bp_part);
         bulk_g2s(smem_u32(st + 2 * g_piece), src, 2u * P.bp_part, bar);
       }
-      store_chunk<CH>(st, st + g_piece, r, buf[0], c, units, P.kind_bf16, P.split);
+      store_chunk<CH>(st, st + g_piece, r, buf[0], c, units, kBF16, kSplit);
       if (c == nch - 1) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&full_bar[s]));
@@ -431,14 +436,14 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
             const uint32_t acc_on = kg > 0 ? 1u : 0u;
             if (P.merged) {
               // columns [0, npad): hi*hi; [npad, 2 npad): hi*lo, then lo*hi added
-              mma_issue(P.kind_bf16, d, da_hi + ao, db_hi + bo, P.idesc2, acc_on);
-              mma_issue(P.kind_bf16, dc, da_lo + ao, db_hi + bo, P.idesc, 1u);
-            } else if (P.split) {
-              mma_issue(P.kind_bf16, dc, da_lo + ao, db_hi + bo, P.idesc, acc_on);
-              mma_issue(P.kind_bf16, dc, da_hi + ao, db_lo + bo, P.idesc, 1u);
-              mma_issue(P.kind_bf16, d, da_hi + ao, db_hi + bo, P.idesc, P.dual ? acc_on : 1u);
+              mma_issue(kBF16, d, da_hi + ao, db_hi + bo, P.idesc2, acc_on);
+              mma_issue(kBF16, dc, da_lo + ao, db_hi + bo, P.idesc, 1u);
+            } else if (kSplit) {
+              mma_issue(kBF16, dc, da_lo + ao, db_hi + bo, P.idesc, acc_on);
+              mma_issue(kBF16, dc, da_hi + ao, db_lo + bo, P.idesc, 1u);
+              mma_issue(kBF16, d, da_hi + ao, db_hi + bo, P.idesc, P.dual ? acc_on : 1u);
             } else {
-              mma_issue(P.kind_bf16, d, da_hi + ao, db_hi + bo, P.idesc, acc_on);
+              mma_issue(kBF16, d, da_hi + ao, db_hi + bo, P.idesc, acc_on);
             }
           }
           mma_commit(smem_u32(&empty_bar[s]));
@@ -593,14 +598,22 @@ size_t tc_rows_scratch_bytes(int ns, int K, int batch, int precision) {
   return tr_bprime_bytes(ns, K, batch, precision == TNQ_PREC_BF16X3);
 }
 
+// kernels by [CH == 16][MODE]
+using TrKernel = void (*)(TrParams);
+const TrKernel kTrKernels[2][3] = {
+    {cgemm_tc_rows_kernel<8, 4, 0>, cgemm_tc_rows_kernel<8, 4, 1>, cgemm_tc_rows_kernel<8, 4, 2>},
+    {cgemm_tc_rows_kernel<16, 2, 0>, cgemm_tc_rows_kernel<16, 2, 1>, cgemm_tc_rows_kernel<16, 2, 2>},
+};
+
 cudaError_t tc_rows_prepare() {
   static cudaError_t result = cudaErrorUnknown;
   static std::once_flag once;
   std::call_once(once, [] {
-    result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TR_SMEM_MAX));
-    if (result == cudaSuccess)
-      result = cudaFuncSetAttribute(cgemm_tc_rows_kernel<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int(TR_SMEM_MAX));
+    result = cudaSuccess;
+    for (const auto& row : kTrKernels)
+      for (TrKernel k : row)
+        if (result == cudaSuccess)
+          result = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TR_SMEM_MAX));
   });
   return result;
 }
@@ -687,10 +700,8 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
     const unsigned blocks = unsigned(std::min<long long>((n + 255) / 256, 1024));
     build_bprime_kernel<<<blocks, 256, 0, st>>>(P, reinterpret_cast<uint8_t*>(scratch));
   }
-  if (ch == 8)
-    cgemm_tc_rows_kernel<8, 4><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
-  else
-    cgemm_tc_rows_kernel<16, 2><<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+  const int mode = P.kind_bf16 ? 2 : (P.split ? 1 : 0);
+  kTrKernels[ch == 16 ? 1 : 0][mode]<<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
 
