@@ -130,10 +130,13 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
 
 __device__ __forceinline__ float bf16_val(uint32_t b) { return __uint_as_float(b << 16); }
 
+// Nearest TF32 value (10 stored mantissa bits), ties away from zero: half a
+// unit of the last kept bit is added to the magnitude field and the 13
+// dropped bits are cleared (a carry into the exponent gives the next binade,
+// or infinity past the largest finite value, as the rounding requires).
+// Integer operations on the full-rate ALU pipe; finite inputs.
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 
 // hi/lo words of two reals (x0, x1) packed for one 4-byte slot of a BF16 row.
@@ -482,40 +485,50 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       const size_t obase = size_t(h) * P.ns * P.ng + size_t(g) * P.g_stride;
       const uint32_t base = tmem + lane_addr + uint32_t(b * P.acc_cols);
       // 32 columns (16 outputs) at a time
-      for (int c0 = 0; c0 < P.npad; c0 += 32) {
-        uint32_t v[32];
+      // 32 columns (16 outputs) at a time; the TMEM loads of the next 32
+      // columns are in flight while this group is stored, and the buffer is
+      // released as soon as its last columns are in registers
+      uint32_t v[32], w[32];
+      auto tmem_ld = [&](int c0) {
         TC_LD16(base + c0, v);
         if (c0 + 16 < P.npad) TC_LD16(base + c0 + 16, (v + 16));
         if (P.dual) {
-          uint32_t w[32];
           TC_LD16(base + P.npad + c0, w);
           if (c0 + 16 < P.npad) TC_LD16(base + P.npad + c0 + 16, (w + 16));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+      };
+      tmem_ld(0);
+      for (int c0 = 0; c0 < P.npad; c0 += 32) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        TC_PIN32(v);
+        TC_PIN32(w);
+        float o[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+        for (int j = 0; j < 32; ++j) o[j] = P.dual ? __uint_as_float(v[j]) + __uint_as_float(w[j]) : __uint_as_float(v[j]);
+        if (c0 + 32 < P.npad) {
+          tmem_ld(c0 + 32);
         } else {
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int s = c0 / 2 + j;
           if (s < P.ns) {
-            const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
-            const size_t o = obase + size_t(s) * P.s_stride;
+            const float re = o[2 * j], im = o[2 * j + 1];
+            const size_t o_at = obase + size_t(s) * P.s_stride;
             if (P.acc) {
-              double2 a = P.acc[o];
+              double2 a = P.acc[o_at];
               a.x += double(re);
               a.y += double(im);
-              P.acc[o] = a;
+              P.acc[o_at] = a;
             } else {
-              P.C[o] = make_float2(re, im);
+              P.C[o_at] = make_float2(re, im);
             }
           }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
       if (++b == P.nacc) {
         b = 0;
         bph ^= 1;
