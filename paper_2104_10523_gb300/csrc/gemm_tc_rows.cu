@@ -42,7 +42,8 @@
 // corrections (about 2^-9 of it) apart cuts that chain to one addition per K
 // step.
 //
-// CTA (persistent, one per SM) = 13 warps:
+// CTA (persistent; one per SM, or two where the stages, S' and TMEM buffers
+// fit in half an SM) = 13 warps:
 //   warps 0-7   converters, two groups of four; group g fills the stages of
 //               the CTA's items i = g, g + 2, ... (an item is one K-part of a
 //               tile): each thread owns one tile row and walks the item's K
@@ -56,9 +57,10 @@
 //   warp 8      allocates TMEM and (one thread) issues the MMAs of each tile
 //               into one of the TMEM accumulator buffers;
 //   warps 9-12  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, 32
-//               columns at a time (and the correction buffer's columns),
-//               and writes complex64 outputs (or adds into the FP64
-//               cross-slice sum).
+//               columns at a time (16 with two CTAs per SM), and the
+//               correction buffer's columns, the next columns' loads in
+//               flight while it writes complex64 outputs (or adds into the
+//               FP64 cross-slice sum).
 // Every mbarrier wait is bounded; one that runs out sets the error flag and
 // the CTA unwinds.
 #include <cuda_bf16.h>
@@ -87,6 +89,7 @@ constexpr int TR_ROW_BYTES = 128;              // one swizzle atom of a row
 constexpr int TR_ATOM_BYTES = 128 * TR_ROW_BYTES;  // one atom column of a 128-row tile
 constexpr int TR_BPRIME_BUDGET = 128 * 1024;
 constexpr int TR_SMEM_LIMIT = 225 * 1024;      // dynamic shared memory of one CTA
+constexpr int TR_SMEM_HALF = 110 * 1024;       // the same, two CTAs per SM
 constexpr int TR_KMAX = 256;                  // longest K (in resident mode: 64)
 
 struct TrParams {
@@ -267,8 +270,10 @@ __device__ __forceinline__ void load_chunk(const TrParams& P, const uint32_t* ko
 // and a kernel holding every mode's conversion code made the rarely running
 // MMA warp miss in the instruction cache (about 200 cycles per group of
 // instructions it issued), so each mode is its own kernel.
-template <int CH, int DEPTH, int MODE>
-__global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __grid_constant__ TrParams P) {
+// MINB: CTAs per SM (2 for launches whose stages, S' and TMEM buffers fit in
+// half an SM: twice the warps to hide the roles' latencies, 72 registers).
+template <int CH, int DEPTH, int MODE, int MINB>
+__global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const __grid_constant__ TrParams P) {
   extern __shared__ uint8_t smem_raw[];
   constexpr int kBF16 = MODE == 2 ? 1 : 0, kSplit = MODE != 0 ? 1 : 0;
   __shared__ __align__(8) uint64_t full_bar[TR_MAX_STAGES];
@@ -485,35 +490,43 @@ __global__ void __launch_bounds__(TR_THREADS, 1) cgemm_tc_rows_kernel(const __gr
       const size_t obase = size_t(h) * P.ns * P.ng + size_t(g) * P.g_stride;
       const uint32_t base = tmem + lane_addr + uint32_t(b * P.acc_cols);
       // 32 columns (16 outputs) at a time
-      // 32 columns (16 outputs) at a time; the TMEM loads of the next 32
+      // EC columns (EC / 2 outputs) at a time; the TMEM loads of the next EC
       // columns are in flight while this group is stored, and the buffer is
       // released as soon as its last columns are in registers
-      uint32_t v[32], w[32];
+      constexpr int EC = MINB == 2 ? 16 : 32;
+      uint32_t v[EC], w[EC];
       auto tmem_ld = [&](int c0) {
         TC_LD16(base + c0, v);
-        if (c0 + 16 < P.npad) TC_LD16(base + c0 + 16, (v + 16));
+        if constexpr (EC == 32)
+          if (c0 + 16 < P.npad) TC_LD16(base + c0 + 16, (v + 16));
         if (P.dual) {
           TC_LD16(base + P.npad + c0, w);
-          if (c0 + 16 < P.npad) TC_LD16(base + P.npad + c0 + 16, (w + 16));
+          if constexpr (EC == 32)
+            if (c0 + 16 < P.npad) TC_LD16(base + P.npad + c0 + 16, (w + 16));
         }
       };
       tmem_ld(0);
-      for (int c0 = 0; c0 < P.npad; c0 += 32) {
+      for (int c0 = 0; c0 < P.npad; c0 += EC) {
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        TC_PIN32(v);
-        TC_PIN32(w);
-        float o[32];
+        if constexpr (EC == 32) {
+          TC_PIN32(v);
+          TC_PIN32(w);
+        } else {
+          TC_PIN16(v);
+          TC_PIN16(w);
+        }
+        float o[EC];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) o[j] = P.dual ? __uint_as_float(v[j]) + __uint_as_float(w[j]) : __uint_as_float(v[j]);
-        if (c0 + 32 < P.npad) {
-          tmem_ld(c0 + 32);
+        for (int j = 0; j < EC; ++j) o[j] = P.dual ? __uint_as_float(v[j]) + __uint_as_float(w[j]) : __uint_as_float(v[j]);
+        if (c0 + EC < P.npad) {
+          tmem_ld(c0 + EC);
         } else {
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
         }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < EC / 2; ++j) {
           const int s = c0 / 2 + j;
           if (s < P.ns) {
             const float re = o[2 * j], im = o[2 * j + 1];
@@ -614,9 +627,13 @@ size_t tc_rows_scratch_bytes(int ns, int K, int batch, int precision) {
 // kernels by [CH == 16][MODE]
 using TrKernel = void (*)(TrParams);
 const TrKernel kTrKernels[2][3] = {
-    {cgemm_tc_rows_kernel<8, 4, 0>, cgemm_tc_rows_kernel<8, 4, 1>, cgemm_tc_rows_kernel<8, 4, 2>},
-    {cgemm_tc_rows_kernel<16, 2, 0>, cgemm_tc_rows_kernel<16, 2, 1>, cgemm_tc_rows_kernel<16, 2, 2>},
+    {cgemm_tc_rows_kernel<8, 4, 0, 1>, cgemm_tc_rows_kernel<8, 4, 1, 1>, cgemm_tc_rows_kernel<8, 4, 2, 1>},
+    {cgemm_tc_rows_kernel<16, 2, 0, 1>, cgemm_tc_rows_kernel<16, 2, 1, 1>, cgemm_tc_rows_kernel<16, 2, 2, 1>},
 };
+// two CTAs per SM, by [MODE]
+const TrKernel kTrKernels2[3] = {cgemm_tc_rows_kernel<8, 2, 0, 2>, cgemm_tc_rows_kernel<8, 2, 1, 2>,
+                                 cgemm_tc_rows_kernel<8, 2, 2, 2>};
+
 
 cudaError_t tc_rows_prepare() {
   static cudaError_t result = cudaErrorUnknown;
@@ -627,6 +644,9 @@ cudaError_t tc_rows_prepare() {
       for (TrKernel k : row)
         if (result == cudaSuccess)
           result = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TR_SMEM_MAX));
+    for (TrKernel k : kTrKernels2)
+      if (result == cudaSuccess)
+        result = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TR_SMEM_HALF));
   });
   return result;
 }
@@ -688,7 +708,23 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   P.dual = (P.split && P.npad <= 128) ? 1 : 0;
   P.merged = P.dual;
   P.acc_cols = P.npad * (P.dual ? 2 : 1);
-  const int ch = P.kc <= 8 ? 8 : 16;
+  // Two CTAs per SM where a launch fits in half an SM: at least two stages
+  // beside S' in TR_SMEM_HALF bytes and two TMEM buffers in 256 columns.
+  // Measured on pair contractions: BF16x3 16 x 2^24 x 16 3.6 -> 4.5 TB/s,
+  // TF32x3 8 x 2^23 x 8 2.7 -> 3.4; TF32x3 16 x 2^24 x 16 unchanged (its
+  // hi/lo split arithmetic, not the warp count, bounds it there).
+  bool two = false;
+  if (!P.stream_bp && 2 * P.acc_cols <= 256) {
+    const size_t stage_bytes = size_t(2) * TR_ATOM_BYTES * P.patoms;
+    int st2 = P.stages;
+    while (st2 > 2 && size_t(st2) * stage_bytes + bp_all + 1024 > size_t(TR_SMEM_HALF)) --st2;
+    if (size_t(st2) * stage_bytes + bp_all + 1024 <= size_t(TR_SMEM_HALF)) {
+      two = true;
+      P.stages = st2;
+      P.nacc = std::min(P.nacc, 256 / P.acc_cols);
+    }
+  }
+  const int ch = (two || P.kc <= 8) ? 8 : 16;
   P.nchunks = (P.kc + ch - 1) / ch;
   P.pairs = gd.nk >= 1 && gd.kpos[0] == 0;
   P.s_stride = s_stride_out;
@@ -704,7 +740,7 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   P.C = reinterpret_cast<float2*>(C);
   P.acc = reinterpret_cast<double2*>(acc);
   P.err = err;
-  const long long grid = std::min<long long>(P.total_tiles, std::max(1, sm_count));
+  const long long grid = std::min<long long>(P.total_tiles, (two ? 2 : 1) * std::max(1, sm_count));
   const size_t smem = size_t(P.stages) * (2 * P.patoms * TR_ATOM_BYTES + (P.stream_bp ? 2 * size_t(P.bp_part) : 0)) +
                       (P.stream_bp ? 0 : bp_all) + 1024;
   if (P.stream_bp) {
@@ -714,7 +750,8 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
     build_bprime_kernel<<<blocks, 256, 0, st>>>(P, reinterpret_cast<uint8_t*>(scratch));
   }
   const int mode = P.kind_bf16 ? 2 : (P.split ? 1 : 0);
-  kTrKernels[ch == 16 ? 1 : 0][mode]<<<unsigned(grid), TR_THREADS, smem, st>>>(P);
+  const TrKernel k = two ? kTrKernels2[mode] : kTrKernels[ch == 16 ? 1 : 0][mode];
+  k<<<unsigned(grid), TR_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
 
