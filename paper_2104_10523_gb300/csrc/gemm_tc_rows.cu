@@ -1,7 +1,7 @@
 // Tall-skinny complex GEMM on the tcgen05 tensor cores, sm_103a.
 //
 // Steps of the contraction sequence (Sec. 3.1) whose one operand is small
-// (ns <= 128 rows) and whose contracted extent is short (K <= 64) but whose
+// (ns <= 128 rows) and whose contracted extent is short (K <= 256) but whose
 // other operand G is large (ng rows, up to 2^24 and more) do 8 * ns real flops
 // per byte of G: too few for a tensor-core tile built the ordinary way (the
 // 2 * ns-row expansion of the small operand would fill part of a 128-row MMA
@@ -34,13 +34,13 @@
 // stays in L2) and each stage receives the K-part of it that its MMAs read, by
 // a bulk copy that completes on the stage's barrier.
 //
-// In the split modes the product hi*hi accumulates into one TMEM buffer
-// and the two correction products hi*lo, lo*hi into a second one beside it
-// (hi*hi and hi*lo are one MMA); the epilogue adds them in FP32 registers.  The tensor-memory accumulator adds each MMA's
-// result with truncation toward zero, so a chain of additions into the large
-// accumulator shrinks it by about half an ulp per addition; keeping the
-// corrections (about 2^-9 of it) apart cuts that chain to one addition per K
-// step.
+// In the split modes the product hi*hi accumulates into one TMEM buffer and
+// the two correction products hi*lo, lo*hi into a second one beside it (hi*hi
+// and hi*lo are one MMA); the epilogue adds them in FP32 registers.  The
+// tensor-memory accumulator adds each MMA's result with truncation toward
+// zero, so a chain of additions into the large accumulator shrinks it by about
+// half an ulp per addition; keeping the corrections (about 2^-9 of it) apart
+// cuts that chain to one addition per K step.
 //
 // CTA (persistent; one per SM, or two where the stages, S' and TMEM buffers
 // fit in half an SM) = 13 warps:
