@@ -333,51 +333,64 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
     // ---------------- converters: group grp fills the stages of items grp, grp+2, ...
     // CTA-local item j is K-part j % kparts of the CTA's tile j / kparts
     // (global tile blockIdx.x + (j / kparts) * gridDim.x); it uses stage
-    // j % stages, phase (j / stages) & 1.
+    // j % stages, phase (j / stages) & 1.  The cursors below carry these
+    // quotients and remainders from item to item instead of dividing.
     const int grp = warp >> 2, r = (warp & 3) * 32 + lane;
     const int nhi = P.gd.nrow - 7;
     const int nch = P.nchunks, units = 2 * P.nks_part;
+    const uint32_t nst = uint32_t(P.stages);
     size_t soff = 0;
     for (int j = 0; j < P.gd.n_slice; ++j)
       if (P.gd.slice_src[j] >= 0 && ((P.slice_id >> j) & 1)) soff |= size_t(1) << P.gd.slice_src[j];
     const size_t lo = soff | deposit(r, P.gd.rowpos, 7);
-    auto row_base = [&](uint32_t t) {
-      const uint32_t h = t / tph, g0 = (t - h * tph) * 128u;
-      return lo | deposit(((long long)h * P.ng + g0) >> 7, P.gd.rowpos + 7, nhi);
+    // row r of tile t is row 128 t + r of the (batch-major) row index, whose
+    // bits above the lowest 7 are t itself
+    auto row_base = [&](uint32_t t) { return lo | deposit((long long)t, P.gd.rowpos + 7, nhi); };
+    // item cursor: K-part and tile of item j, advanced by the group stride 2
+    struct ItemCursor {
+      uint32_t kp, tile;
     };
-    auto item_tile = [&](uint32_t j) { return blockIdx.x + (j / uint32_t(kparts)) * gridDim.x; };
+    auto first_item = [&]() {
+      ItemCursor q{uint32_t(grp), blockIdx.x};
+      while (q.kp >= uint32_t(kparts)) {
+        q.kp -= uint32_t(kparts);
+        q.tile += gridDim.x;
+      }
+      return q;
+    };
+    auto next_item = [&](ItemCursor& q) {
+      q.kp += 2;
+      while (q.kp >= uint32_t(kparts)) {
+        q.kp -= uint32_t(kparts);
+        q.tile += gridDim.x;
+      }
+    };
     // items (item, chunk c) in order: the loads of the next DEPTH chunks are in
     // flight while one is split and stored.
-    uint32_t jl = uint32_t(grp);  // load cursor: item, chunk, its tile's row base
-    uint32_t tl = item_tile(jl);
+    ItemCursor ql = first_item();  // load cursor: item, chunk, its tile's row base
     int cl = 0;
-    size_t bl = tl < total ? row_base(tl) : 0;
+    size_t bl = ql.tile < total ? row_base(ql.tile) : 0;
     auto advance_load = [&]() {
       if (++cl == nch) {
         cl = 0;
-        jl += 2;
-        const uint32_t tn = item_tile(jl);
-        if (tn != tl) {
-          tl = tn;
-          bl = tl < total ? row_base(tl) : 0;
-        }
+        const uint32_t t0 = ql.tile;
+        next_item(ql);
+        if (ql.tile != t0) bl = ql.tile < total ? row_base(ql.tile) : 0;
       }
     };
     float2 buf[DEPTH + 1][CH];
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d) {
-      if (tl < total) load_chunk<CH>(P, koff, bl, int(jl % uint32_t(kparts)), cl, buf[d]);
+      if (ql.tile < total) load_chunk<CH>(P, koff, bl, int(ql.kp), cl, buf[d]);
       advance_load();
     }
-    uint32_t jc = uint32_t(grp);  // convert cursor
+    ItemCursor qc = first_item();  // convert cursor
+    uint32_t s = uint32_t(grp), ph = 0;  // its stage and phase: j % stages, (j / stages) & 1
     int c = 0;
-    while (item_tile(jc) < total) {
-      // item jc uses stage jc % stages in phase (jc / stages) & 1; its empty
-      // wait orders it after the MMAs of item jc - stages, whichever group
-      // converted that one, so any stage count works
-      const int s = int(jc % uint32_t(P.stages));
-      const uint32_t ph = (jc / uint32_t(P.stages)) & 1u;
-      if (tl < total) load_chunk<CH>(P, koff, bl, int(jl % uint32_t(kparts)), cl, buf[DEPTH]);
+    while (qc.tile < total) {
+      // the empty wait orders this item after the MMAs of item j - stages,
+      // whichever group converted that one, so any stage count works
+      if (ql.tile < total) load_chunk<CH>(P, koff, bl, int(ql.kp), cl, buf[DEPTH]);
       advance_load();
       if (c == 0 && !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1)) {
         atomicOr(P.err, 1);
@@ -387,8 +400,7 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
       if (c == 0 && P.stream_bp && r == 0) {
         // S' hi and lo of this item's K-part, copied into the stage by the bulk
         // copy engine; the stage completes when both copies have landed
-        const uint32_t tt = item_tile(jc), kp = jc % uint32_t(kparts);
-        const uint8_t* src = P.bp_glob + size_t(tt / tph) * bp_entry + size_t(kp) * 2u * P.bp_part;
+        const uint8_t* src = P.bp_glob + size_t(qc.tile / tph) * bp_entry + size_t(qc.kp) * 2u * P.bp_part;
         const uint32_t bar = smem_u32(&full_bar[s]);
         mbar_expect_tx(bar, 2u * P.bp_part);
         bulk_g2s(smem_u32(st + 2 * g_piece), src, 2u * P.bp_part, bar);
@@ -404,7 +416,12 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
         for (int j = 0; j < CH; ++j) buf[d][j] = buf[d + 1][j];
       if (++c == nch) {
         c = 0;
-        jc += 2;
+        next_item(qc);
+        s += 2;
+        while (s >= nst) {
+          s -= nst;
+          ph ^= 1u;
+        }
       }
     }
   } else if (warp == TR_MMA_WARP) {
@@ -731,7 +748,8 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   P.g_stride = g_stride_out;
   P.tiles_per_h = ng / 128;
   P.total_tiles = (long long)P.tiles_per_h * batch;
-  if (P.total_tiles + 2ll * std::max(1, sm_count) > 0xffffffffll) return cudaErrorNotSupported;  // 32-bit tile counters
+  // 32-bit tile counters: cursors run up to 2 items (4 grid strides) past the end
+  if (P.total_tiles + 8ll * std::max(1, sm_count) > 0xffffffffll) return cudaErrorNotSupported;
   P.slice_id = slice_id;
   // instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1), K-major, N >> 3, M >> 4
   const uint32_t fmt = P.kind_bf16 ? 1u : 2u;
