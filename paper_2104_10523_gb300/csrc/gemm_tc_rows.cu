@@ -91,6 +91,7 @@ constexpr int TR_BPRIME_BUDGET = 128 * 1024;
 constexpr int TR_SMEM_LIMIT = 225 * 1024;      // dynamic shared memory of one CTA
 constexpr int TR_SMEM_HALF = 110 * 1024;       // the same, two CTAs per SM
 constexpr int TR_KMAX = 256;                  // longest K (in resident mode: 64)
+constexpr int TR_ROWTAB_DIGITS = 7;           // 4-bit digits of a tile index (nrow <= 35)
 
 struct TrParams {
   const float2* S;        // small operand [batch][ns][K]
@@ -116,6 +117,7 @@ struct TrParams {
   int kind_bf16;          // 1: BF16 parts, kind::f16; 0: TF32 parts, kind::tf32
   int split;              // 1: three products (hi/lo); 0: one TF32 product
   int pairs;              // the lowest stored bit of G is K bit 0: 16-byte loads
+  int row_tab;            // 1: every stored position of the row bits above 7 is below 32 (digit table)
   long long s_stride, g_stride;
   int tiles_per_h;        // ng / 128
   long long total_tiles;
@@ -240,6 +242,30 @@ __global__ void build_bprime_kernel(const __grid_constant__ TrParams P, uint8_t*
   build_bprime(P, dst, int(blockIdx.x * blockDim.x + threadIdx.x), int(gridDim.x * blockDim.x));
 }
 
+// Tile t = h * tph + gt (batch entry h, tile gt within it), stepped by the
+// grid stride without a division in the common case (stride < 2 tph).
+struct TileHG {
+  uint32_t h, gt;
+};
+
+__device__ __forceinline__ TileHG tile_hg(uint32_t t, uint32_t tph) {
+  const uint32_t h = t / tph;
+  return TileHG{h, t - h * tph};
+}
+
+__device__ __forceinline__ void tile_step(TileHG& q, uint32_t step, uint32_t tph) {
+  q.gt += step;
+  if (q.gt >= tph) {
+    if (q.gt < 2 * tph) {
+      q.gt -= tph;
+      ++q.h;
+    } else {
+      q.h += q.gt / tph;
+      q.gt %= tph;
+    }
+  }
+}
+
 __device__ __forceinline__ size_t deposit(long long v, const int* pos, int n) {
   size_t o = 0;
   for (int j = 0; j < n; ++j)
@@ -283,6 +309,9 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
   __shared__ __align__(8) uint64_t final_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t koff[TR_KMAX];
+  // deposit of each 4-bit digit of a tile index into the stored positions of
+  // the row bits above the lowest 7 (used when every position is below 32)
+  __shared__ uint32_t rowtab[TR_ROWTAB_DIGITS][16];
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // a stage: G hi and lo of one K-part, then (streamed mode) S' hi and lo of that part
@@ -313,6 +342,16 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
       if ((kk >> j) & 1) o |= 1u << P.gd.kpos[j];
     koff[kk] = o;
   }
+  const int nhi_all = P.gd.nrow - 7, ndig = (nhi_all + 3) / 4;
+  const bool use_rowtab = P.row_tab != 0;
+  if (use_rowtab)
+    for (int e = threadIdx.x; e < ndig * 16; e += blockDim.x) {
+      const int n = e >> 4, v = e & 15;
+      uint32_t o = 0;
+      for (int b = 0; b < 4 && 4 * n + b < nhi_all; ++b)
+        if ((v >> b) & 1) o |= 1u << P.gd.rowpos[7 + 4 * n + b];
+      rowtab[n][v] = o;
+    }
   if (warp < TR_CONV_WARPS && !P.stream_bp) build_bprime(P, bprime, threadIdx.x, 32 * TR_CONV_WARPS);
   if (warp == TR_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -345,7 +384,12 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
     const size_t lo = soff | deposit(r, P.gd.rowpos, 7);
     // row r of tile t is row 128 t + r of the (batch-major) row index, whose
     // bits above the lowest 7 are t itself
-    auto row_base = [&](uint32_t t) { return lo | deposit((long long)t, P.gd.rowpos + 7, nhi); };
+    auto row_base = [&](uint32_t t) {
+      if (!use_rowtab) return lo | deposit((long long)t, P.gd.rowpos + 7, nhi);
+      size_t o = lo;
+      for (int n = 0; n < ndig; ++n) o |= rowtab[n][(t >> (4 * n)) & 15u];
+      return o;
+    };
     // item cursor: K-part and tile of item j, advanced by the group stride 2
     struct ItemCursor {
       uint32_t kp, tile;
@@ -431,12 +475,13 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
       uint32_t sph = 0, bph = 0;  // phases of the stage ring and of the accumulator ring
       bool drained = false;       // every accumulator buffer has been used once
       bool ok = true;
-      for (uint32_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      TileHG hg = tile_hg(blockIdx.x, tph);
+      for (uint32_t t = blockIdx.x; t < total && ok; t += gridDim.x, tile_step(hg, gridDim.x, tph)) {
         if (drained && !mbar_wait(smem_u32(&acc_empty[b]), bph ^ 1)) {
           atomicOr(P.err, 1);
           break;
         }
-        const uint32_t h = t / tph;
+        const uint32_t h = hg.h;
         const uint32_t d = tmem + uint32_t(b * P.acc_cols);
         const uint32_t dc = P.dual ? d + uint32_t(P.npad) : d;  // correction products
         for (int kp = 0; kp < kparts; ++kp) {
@@ -495,15 +540,16 @@ __global__ void __launch_bounds__(TR_THREADS, MINB) cgemm_tc_rows_kernel(const _
     const int row = quarter * 32 + lane;
     int b = 0;
     uint32_t bph = 0;
-    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+    TileHG hg = tile_hg(blockIdx.x, tph);
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, tile_step(hg, gridDim.x, tph)) {
       const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[b]), bph));
       if (!ok) {
         if (lane == 0) atomicOr(P.err, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t h = t / tph;
-      const uint32_t g = (t - h * tph) * 128u + uint32_t(row);
+      const uint32_t h = hg.h;
+      const uint32_t g = hg.gt * 128u + uint32_t(row);
       const size_t obase = size_t(h) * P.ns * P.ng + size_t(g) * P.g_stride;
       const uint32_t base = tmem + lane_addr + uint32_t(b * P.acc_cols);
       // 32 columns (16 outputs) at a time
@@ -744,6 +790,9 @@ cudaError_t launch_tc_rows_one(const void* Ssmall, const void* Gsrc, const Gathe
   const int ch = (two || P.kc <= 8) ? 8 : 16;
   P.nchunks = (P.kc + ch - 1) / ch;
   P.pairs = gd.nk >= 1 && gd.kpos[0] == 0;
+  P.row_tab = gd.nrow - 7 <= 4 * TR_ROWTAB_DIGITS ? 1 : 0;
+  for (int j = 7; j < gd.nrow; ++j)
+    if (gd.rowpos[j] >= 32) P.row_tab = 0;
   P.s_stride = s_stride_out;
   P.g_stride = g_stride_out;
   P.tiles_per_h = ng / 128;
