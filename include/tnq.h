@@ -321,7 +321,7 @@ tnq_status tnq_contract_pair_noalloc(tnq_ctx* ctx, const void* A, int ra, const 
  * on the tensor cores is timed (CUDA events, best of `reps` after a warm-up run,
  * on the plan's workspace) both there and on the CUDA cores (row-streaming,
  * dot or tiled FP32 kernel); a tall-skinny step (one operand of at most 128
- * rows, K <= 64) is also timed with the large operand gathered, split and
+ * rows, K <= 256) is also timed with the large operand gathered, split and
  * multiplied in one tensor-core kernel.  The fastest choice is kept in the plan for
  * that precision; later calls at that precision follow it (and re-capture
  * their graph).  Results are unchanged in meaning (each choice meets the
